@@ -1,0 +1,198 @@
+"""The oracle pinned to what the paper and the mathematics fix (CPU only).
+
+Pins, each independent of the oracle's own code:
+  * radicals of the integers printed in Tables 1 and 2, from their factorisations;
+  * radicals from sympy's factoriser (a library routine) on random and adversarial x;
+  * structural invariants of rad (squarefree, divides x, same prime support);
+  * Algorithm 1's sieve agrees with the trial-division definition on segments
+    whose edges sit on prime powers;
+  * pair sets equal Theorem 1's closed forms (brute force, Algorithm 2, CRT);
+  * Algorithm 2 and the CRT enumeration, two different methods, agree;
+  * every Theorem 1 pair passes the per-kind necessary conditions.
+A planted-mistake test builds the oracle with each ORC_MUTANT hook and checks
+that these pins catch every one of them.
+"""
+import math
+import random
+
+import numpy as np
+import pytest
+
+from paper_pins import THEOREM1_BOUND, table_rows, theorem1_pairs
+
+
+def _rad_from_fact(fd):
+    return math.prod(fd.keys())
+
+
+# ---------------------------------------------------------------------------
+# pins as functions returning a list of failures (reused by the mutant test)
+# ---------------------------------------------------------------------------
+
+def pin_tables(o):
+    bad = []
+    for kind, m, n, facts in table_rows():
+        for x, fd in facts.items():
+            if math.prod(p**e for p, e in fd.items()) != x:
+                bad.append(f"table factorisation of {x} does not multiply out")
+            if o.rad_td(x) != _rad_from_fact(fd):
+                bad.append(f"rad_td({x}) = {o.rad_td(x)} != {_rad_from_fact(fd)}")
+    return bad
+
+
+def pin_sieve_edges(o):
+    bad = []
+    cases = [(1, 9), (1, 5000), (9, 100), (2**32 - 3000, 6000), (2**40 - 2**12, 2**13),
+             (1048573**2 - 100, 101), (1048573**2, 64), (3**25 - 7, 50), (65537**2 - 1, 3),
+             (1_400_000_000_000 - 4096, 4096)]
+    for start, length in cases:
+        got = o.rad_sieve(start, length)
+        want = o.rad_td_array(start, length)
+        if not np.array_equal(got, want):
+            i = int(np.nonzero(got != want)[0][0])
+            bad.append(f"sieve({start},{length})[{i}] = {got[i]} != {want[i]}")
+    return bad
+
+
+def pin_brute(o):
+    got = o.pairs_brute(1 << 12)
+    want = theorem1_pairs(1, 1 << 12)
+    return [] if got == want else [f"brute(2^12) {got} != {want}"]
+
+
+def pin_sort(o):
+    got = o.pairs_sort(1 << 20)
+    want = theorem1_pairs(1, 1 << 20)
+    return [] if got == want else [f"sort(2^20) {got} != {want}"]
+
+
+def pin_crt(o):
+    bad = []
+    windows = [(1, 1 << 20), (2**40 - 2**21 - 2**19, 2**40 + 2**21 + 2**19),
+               (17179607040 - 5000, 17180131328 + 5000)]
+    for lo, hi in windows:
+        for kinds in (1, 2, 3):
+            got = o.pairs_crt(lo, hi, kinds)
+            want = theorem1_pairs(lo, hi, kinds)
+            if got != want:
+                bad.append(f"crt[{lo},{hi}) kinds={kinds}: {got} != {want}")
+    return bad
+
+
+ALL_PINS = [pin_tables, pin_sieve_edges, pin_brute, pin_sort, pin_crt]
+
+
+# ---------------------------------------------------------------------------
+# the tests
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("pin", ALL_PINS, ids=lambda f: f.__name__)
+def test_pin(orc, pin):
+    assert pin(orc) == []
+
+
+def test_theorem1_matches_tables():
+    """The closed forms of Theorem 1 list exactly the rows of Tables 1 and 2."""
+    rows = sorted(((m, n, kind) for kind, m, n, _ in table_rows()), key=lambda p: (p[1], p[0], p[2]))
+    assert rows == theorem1_pairs()
+
+
+def test_table_rows_are_pairs(orc):
+    for kind, m, n, _ in table_rows():
+        a, b, c, d = orc.rad_td(m), orc.rad_td(m + 1), orc.rad_td(n), orc.rad_td(n + 1)
+        if kind == 1:
+            assert (a, b) == (c, d)
+        else:
+            assert (a, b) == (d, c)
+
+
+def test_rad_td_vs_sympy(orc):
+    sympy = pytest.importorskip("sympy")
+    rng = random.Random(2506_01099)
+    xs = [1, 2, 3, 4, 8, 9, 2**40, 2**41 + 1, 3**26, 1048573**2, 1048573 * 1048571, 999983**2 * 4]
+    xs += [2**k + d for k in range(2, 42) for d in (-1, 1)]
+    xs += [rng.randrange(1, 2**42) for _ in range(300)]
+    xs += [rng.randrange(1, 2**20) ** 2 for _ in range(50)]
+    for x in xs:
+        assert orc.rad_td(x) == math.prod(sympy.primefactors(x)), x
+
+
+def test_rad_invariants(orc):
+    rng = random.Random(7)
+    for _ in range(2000):
+        x = rng.randrange(1, 2**42)
+        r = orc.rad_td(x)
+        assert x % r == 0
+        # same prime support: x divides rad(x)^e for e = log2(x)
+        assert pow(r, 42, x) == 0 or x == 1
+        # squarefree: no prime square below 2^11 divides it, and rad is idempotent
+        assert all(r % (p * p) for p in (2, 3, 5, 7, 11, 13, 1009, 2039))
+        assert orc.rad_td(r) == r
+        assert orc.sq_td(x) * r == x
+    assert orc.rad_td(1) == 1
+
+
+def test_sort_equals_crt(orc):
+    """Algorithm 2 (sorting all 2-sets) and the CRT enumeration agree on [1, 2^22)."""
+    assert orc.pairs_sort(1 << 22) == orc.pairs_crt(1, 1 << 22)
+
+
+def test_crt_window_at_2p40(orc):
+    """[2^40, 2^40 + 2^30) holds exactly one pair, of the second kind."""
+    lo = 2**40
+    got = orc.pairs_crt(lo, lo + (1 << 30))
+    assert got == [(1048577, 1099513724928, 2)]
+    assert got == theorem1_pairs(lo, lo + (1 << 30))
+
+
+def test_crt_empty_window_below_bound(orc):
+    assert orc.pairs_crt(THEOREM1_BOUND - (1 << 26), THEOREM1_BOUND) == []
+
+
+def test_necessary_conditions_hold_for_every_pair(orc):
+    """Each Theorem 1 pair passes its kind's filter; counts are monotone in the window."""
+    for m, n, kind in theorem1_pairs(1, 1 << 40):
+        c1, c2 = orc.filter_counts(n, n + 1, kind)
+        assert (c1 if kind == 1 else c2) == 1, (m, n, kind)
+    a1, a2 = orc.filter_counts(1, 1 << 20)
+    b1, b2 = orc.filter_counts(1, 1 << 21)
+    assert b1 >= a1 and b2 >= a2 and a2 >= 0
+
+
+def test_hash_keys_cover_pair_members(orc):
+    """Every member of a pair with n < S has rad(x)rad(x+1) <= 2S (the hash insert rule)."""
+    S = 1 << 16
+    assert orc.hash_keys(S) >= len({x for m, n, _ in theorem1_pairs(1, S) for x in (m, n)})
+    for m, n, _ in theorem1_pairs(1, S):
+        for x in (m, n):
+            assert orc.rad_td(x) * orc.rad_td(x + 1) <= 2 * S
+
+
+def test_nprimes(orc):
+    """pi(x) at a few textbook values."""
+    assert orc.nprimes_upto(100) == 25
+    assert orc.nprimes_upto(2**12) == 564
+    assert orc.nprimes_upto(2**16) == 6542
+    assert orc.nprimes_upto(10**6) == 78498
+
+
+MUTANTS = {1: "rad_td drops the last prime cofactor", 2: "Alg. 1 misses the multiple at start",
+           3: "Alg. 1 starts at exponent 1", 4: "Alg. 2 kind rule inverted",
+           5: "CRT second kind m = j*ab - n", 6: "first-kind inequality used for the second kind",
+           7: "Alg. 1 sieves primes p < sqrt(S) only", 8: "brute force transposes an operand"}
+
+
+@pytest.mark.parametrize("k", sorted(MUTANTS), ids=lambda k: f"mutant{k}")
+def test_planted_mistake_is_caught(k, tmp_path):
+    import oracle
+
+    mut = oracle.Oracle(oracle.build(mutant=k, out_dir=str(tmp_path)))
+    failures = []
+    for pin in ALL_PINS:  # cheapest first; stop at the first pin that fails
+        try:
+            failures += pin(mut)
+        except Exception as e:  # a mutant may also crash a pin
+            failures.append(repr(e))
+        if failures:
+            break
+    assert failures, f"no pin caught mutant {k}: {MUTANTS[k]}"
