@@ -1,0 +1,215 @@
+/*
+ * benelux.h -- C ABI of libbenelux, a GB300 (sm_103a) search for Benelux pairs.
+ *
+ * Method: Hercher, "On one of Erdos' Problems -- An Efficient Search for
+ * Benelux Pairs" (arXiv 2506.01099).
+ *
+ *   rad(x)       product of the distinct primes dividing x; rad(1) = 1 (Sec. 2.1)
+ *   first kind   1 <= m < n with rad(m) = rad(n) and rad(m+1) = rad(n+1) (Sec. 1)
+ *   second kind  1 <= m < n with rad(m) = rad(n+1) and rad(m+1) = rad(n) (Sec. 1)
+ *
+ * A search over an n-range [lo, hi) reports every pair (m, n) of the requested
+ * kinds with lo <= n < hi and any 1 <= m < n: the contract of Algorithm 3
+ * (Sec. 2.2), which reports the pairs whose larger member lies in the chunk.
+ * Pairs come back sorted by (n, m, kind).
+ *
+ * Conventions for every call:
+ *  - Return value: BNX_OK (0) or one of the BNX_E_* codes below; no C++
+ *    exception crosses this boundary.  bnx_strerror() names a code, and
+ *    bnx_last_error() gives the message of the last failure on this thread.
+ *  - `kinds` is a bit mask: 1 = first kind, 2 = second kind, 3 = both.
+ *  - Ranges: 1 <= lo < hi <= max_hi, where max_hi is fixed at bnx_create and is
+ *    at most BNX_MAX_HI = 2^42 (so that 2n and every intermediate fit in 64 bits).
+ *  - Output buffers are owned by the caller.  The library owns its device
+ *    tables and workspace (allocated with cudaMalloc, freed by bnx_destroy).
+ *  - When a pair buffer is too small the call returns BNX_E_TRUNCATED, writes
+ *    the first `cap` pairs and still stores the exact count in *n_out.
+ *  - A context is bound to one device and one CUDA stream; calls on one context
+ *    must not run concurrently.  Different contexts are independent.
+ *  - Synchronous calls (bnx_search, bnx_search_hash, bnx_batch) return after the
+ *    device work is complete.  bnx_rad_segment is asynchronous on the stream.
+ */
+#ifndef BENELUX_H
+#define BENELUX_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BNX_OK 0
+#define BNX_E_ARG 1        /* an argument is out of range or a pointer is NULL */
+#define BNX_E_TRUNCATED 2  /* the output buffer was too small; *n_out is exact */
+#define BNX_E_NOMEM 3      /* a device or host allocation failed, or admission refused */
+#define BNX_E_CUDA 4       /* a CUDA runtime call or kernel launch failed */
+#define BNX_E_TIMEOUT 5    /* a bounded device or host wait gave up */
+#define BNX_E_BUSY 6       /* a served request is not finished yet */
+#define BNX_E_STATE 7      /* the call does not fit the context's state */
+#define BNX_E_OVERFLOW 8   /* a device-side capacity was exceeded */
+
+#define BNX_MAX_HI ((uint64_t)1 << 42)
+
+typedef struct bnx_ctx bnx_ctx;
+
+/* One reported pair.  kind is 1 or 2. */
+typedef struct {
+    uint64_t m, n;
+    uint32_t kind;
+    uint32_t iv; /* index of the interval (bnx_batch) or 0 */
+} bnx_pair;
+
+/* One n-range [lo, hi) with its kind mask and a caller tag. */
+typedef struct {
+    uint64_t lo, hi;
+    uint32_t kinds;
+    uint32_t id;
+} bnx_interval;
+
+/* Tunable launch parameters (all optional in the JSON given to bnx_create). */
+typedef struct {
+    uint32_t tile_log2;    /* shared-memory tile: 2^tile_log2 integers (12..14) */
+    uint32_t seg_tiles;    /* tiles per queue segment (1..64) */
+    uint32_t threads;      /* threads per CTA (256, 512 or 1024) */
+    uint32_t ctas_per_sm;  /* resident CTAs per SM for the persistent grid (0 = occupancy limit) */
+    uint32_t small_q_log2; /* prime powers q <= 2^small_q_log2 are struck in shared
+                              memory, larger ones come from the HBM buckets (8..20) */
+} bnx_tune;
+
+/* Per-call counters of the last search on a context. */
+typedef struct {
+    uint64_t integers;     /* n values searched */
+    uint64_t segments;     /* queue segments processed */
+    uint64_t bucket_hits;  /* large prime-power hits written to the buckets */
+    uint64_t survivors1;   /* n passing the first-kind necessary condition */
+    uint64_t survivors2;   /* n passing the second-kind necessary condition */
+    uint64_t candidates;   /* candidate m values verified */
+    uint64_t pairs;        /* pairs found */
+    uint64_t hash_keys;    /* keys inserted (bnx_search_hash) */
+    float ms_total;        /* device time of the whole call (CUDA events) */
+    float ms_sieve;        /* device time of the sieve kernel launches */
+    uint32_t sieve_launches;
+    uint32_t pad;
+} bnx_stats;
+
+/* ------------------------------------------------------------------------ */
+/* Context                                                                    */
+/* ------------------------------------------------------------------------ */
+
+/* Create a context on `device` for ranges up to max_hi (<= BNX_MAX_HI).  Builds
+ * the device-resident tables of Sec. 3.1 ("the list of primes ... sent to the
+ * GPU" once): every prime p <= sqrt(max_hi) by a device sieve, the prime powers
+ * p^k (k >= 2) <= max_hi, and per-entry constants.  `tune_json` is NULL or a
+ * JSON object with any of the bnx_tune field names; missing fields take the
+ * built-in defaults.  `stream` is a cudaStream_t to run on, or NULL for a new
+ * stream owned by the context.  Errors: BNX_E_ARG, BNX_E_NOMEM, BNX_E_CUDA. */
+int bnx_create(bnx_ctx **out, int device, uint64_t max_hi, const char *tune_json, void *stream);
+
+/* Free every device and host resource of the context (NULL is accepted). */
+void bnx_destroy(bnx_ctx *ctx);
+
+/* Read or replace the tuning of a context (replacing frees cached graphs). */
+int bnx_get_tune(const bnx_ctx *ctx, bnx_tune *out);
+int bnx_set_tune(bnx_ctx *ctx, const bnx_tune *tune);
+
+/* Counters of the last completed search on this context. */
+int bnx_get_stats(const bnx_ctx *ctx, bnx_stats *out);
+
+/* Number of primes <= sqrt(max_hi) held on the device. */
+int bnx_prime_count(const bnx_ctx *ctx, uint64_t *out);
+
+/* ------------------------------------------------------------------------ */
+/* Segment-level calls                                                         */
+/* ------------------------------------------------------------------------ */
+
+/* Radicals of x in [lo, lo+len): rad_out[i] = rad(lo+i) and, when sq_out is not
+ * NULL, sq_out[i] = (lo+i) / rad(lo+i), the product of p^(e-1) over p^e || x.
+ * This is the output of Algorithm 1 (Sec. 2.1), computed by the same
+ * shared-memory tile sieve as the search.  rad_out and sq_out are DEVICE
+ * pointers (uint64_t, len elements, 8-byte aligned); the call is asynchronous
+ * on `stream` (NULL: the context's stream).  1 <= lo, lo + len <= max_hi,
+ * 1 <= len <= 2^31.  Errors: BNX_E_ARG, BNX_E_CUDA. */
+int bnx_rad_segment(bnx_ctx *ctx, uint64_t lo, uint64_t len, uint64_t *rad_out, uint64_t *sq_out, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Searches                                                                    */
+/* ------------------------------------------------------------------------ */
+
+/* Plain path: all pairs with lo <= n < hi.  The range is cut into queue
+ * segments; per segment the tile sieve (Algorithm 1 restated per tile), the key
+ * (rad n, rad n+1) of Sec. 2.1, the exact per-kind necessary conditions forced
+ * by the Chinese remainder theorem (first kind rad(n)rad(n+1) | n - m, second
+ * kind rad(n)rad(n+1) | m + n + 1), warp-ballot compaction of survivors, and
+ * candidate verification.  `out` is a HOST buffer of `cap` pairs.  Blocking.
+ * Errors: BNX_E_ARG, BNX_E_TRUNCATED, BNX_E_NOMEM, BNX_E_CUDA, BNX_E_OVERFLOW. */
+int bnx_search(bnx_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t kinds, bnx_pair *out, size_t cap, size_t *n_out);
+
+/* Full-range search by collision detection, as in Algorithms 2 and 3: all
+ * pairs with m < n < S.  Every x < S whose key (rad x, rad x+1) can belong to a
+ * pair (rad(x)rad(x+1) <= 2S) is inserted into a device open-addressing hash
+ * table keyed by the 2-set; every two integers with equal keys form a pair, of
+ * the first kind when rad(m) = rad(n) (Algorithm 2's rule).  2 <= S <= 2^40.
+ * `out` is a HOST buffer.  Blocking.  Errors as bnx_search. */
+int bnx_search_hash(bnx_ctx *ctx, uint64_t S, uint32_t kinds, bnx_pair *out, size_t cap, size_t *n_out);
+
+/* Batched path: k intervals in one pipeline -- large-prime bucket fill, one
+ * persistent sieve launch pulling segments from a device queue, verification
+ * and a device sort -- replayed from a cached CUDA graph when the batch shape
+ * repeats.  `iv`, `out` and `offsets` are HOST buffers.  On success out holds
+ * the pairs sorted by (interval index, n, m, kind) with bnx_pair.iv set, and
+ * offsets[i] .. offsets[i+1] delimit interval i's pairs (offsets has k+1
+ * entries; may be NULL).  Errors as bnx_search. */
+int bnx_batch(bnx_ctx *ctx, const bnx_interval *iv, size_t k, bnx_pair *out, size_t cap, size_t *n_out,
+              uint64_t *offsets);
+
+/* ------------------------------------------------------------------------ */
+/* Serving: continuous batching of interval requests                          */
+/* ------------------------------------------------------------------------ */
+
+typedef struct {
+    uint32_t max_active;      /* requests on the device at once (slots) */
+    uint32_t pad;
+    uint64_t slice;           /* integers of each active request per iteration */
+    uint64_t mem_budget;      /* bytes of workspace admission may commit (0: 90% of free HBM) */
+} bnx_server_cfg;
+
+/* Start the serving loop on a background host thread.  Each iteration takes
+ * the next slice of every active request, runs them as one batched pipeline,
+ * and admits waiting requests as slots and memory free up.
+ * Errors: BNX_E_ARG, BNX_E_STATE (already running), BNX_E_NOMEM. */
+int bnx_server_start(bnx_ctx *ctx, const bnx_server_cfg *cfg);
+
+/* Queue a request; *ticket identifies it.  Never blocks on the device. */
+int bnx_server_submit(bnx_ctx *ctx, const bnx_interval *iv, uint64_t *ticket);
+
+/* BNX_E_BUSY while the request runs; BNX_OK once done, with its pairs copied to
+ * the host buffer `out` (sorted by (n, m, kind)) and latency_s = completion time
+ * minus submit time.  A finished request is released by the first successful
+ * poll.  BNX_E_ARG for an unknown ticket. */
+int bnx_server_poll(bnx_ctx *ctx, uint64_t ticket, bnx_pair *out, size_t cap, size_t *n_out, double *latency_s);
+
+/* Stop the loop after the current iteration; unfinished requests are dropped. */
+int bnx_server_stop(bnx_ctx *ctx);
+
+/* ------------------------------------------------------------------------ */
+/* Autotuning                                                                 */
+/* ------------------------------------------------------------------------ */
+
+/* Time candidate tunings (tile length, tiles per segment, threads, CTAs per SM,
+ * shared-memory prime-power limit) on the batched path over `k` sample
+ * intervals, keep the fastest in the context, and write it as JSON to
+ * `json_out` (size `json_cap`, may be NULL).  Errors: BNX_E_ARG, BNX_E_CUDA. */
+int bnx_autotune(bnx_ctx *ctx, const bnx_interval *iv, size_t k, int rounds, char *json_out, size_t json_cap);
+
+/* ------------------------------------------------------------------------ */
+/* Errors                                                                      */
+/* ------------------------------------------------------------------------ */
+
+const char *bnx_strerror(int code);
+const char *bnx_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BENELUX_H */

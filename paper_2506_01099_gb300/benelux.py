@@ -1,0 +1,300 @@
+"""Thin ctypes binding of libbenelux (include/benelux.h), same names as the C ABI.
+
+Argument marshalling only: every step of the search runs in the library's CUDA
+kernels.  There is no CPU fallback -- if the library is missing or cannot be
+loaded, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+from . import build as _build
+
+BNX_OK, BNX_E_ARG, BNX_E_TRUNCATED, BNX_E_NOMEM, BNX_E_CUDA = 0, 1, 2, 3, 4
+BNX_E_TIMEOUT, BNX_E_BUSY, BNX_E_STATE, BNX_E_OVERFLOW = 5, 6, 7, 8
+BNX_MAX_HI = 1 << 42
+
+u64, u32, i32, sz, vp = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_size_t, ctypes.c_void_p
+
+
+class bnx_pair(ctypes.Structure):
+    _fields_ = [("m", u64), ("n", u64), ("kind", u32), ("iv", u32)]
+
+
+class bnx_interval(ctypes.Structure):
+    _fields_ = [("lo", u64), ("hi", u64), ("kinds", u32), ("id", u32)]
+
+
+class bnx_tune(ctypes.Structure):
+    _fields_ = [("tile_log2", u32), ("seg_tiles", u32), ("threads", u32), ("ctas_per_sm", u32),
+                ("small_q_log2", u32)]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
+class bnx_stats(ctypes.Structure):
+    _fields_ = [("integers", u64), ("segments", u64), ("bucket_hits", u64), ("survivors1", u64),
+                ("survivors2", u64), ("candidates", u64), ("pairs", u64), ("hash_keys", u64),
+                ("ms_total", ctypes.c_float), ("ms_sieve", ctypes.c_float), ("sieve_launches", u32),
+                ("pad", u32)]
+
+    def as_dict(self):
+        return {f: (float(getattr(self, f)) if t is ctypes.c_float else int(getattr(self, f)))
+                for f, t in self._fields_ if f != "pad"}
+
+
+class bnx_server_cfg(ctypes.Structure):
+    _fields_ = [("max_active", u32), ("pad", u32), ("slice", u64), ("mem_budget", u64)]
+
+
+class BnxError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"bnx error {code}: {msg}")
+        self.code = code
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib(auto_build: bool = True):
+    """Load libbenelux.so (building it first when it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB
+        if auto_build and not _build.up_to_date():
+            path = _build.build()
+        if not os.path.exists(path):
+            raise RuntimeError("libbenelux.so is not built; run paper_2506_01099_gb300.build.build()")
+        L = ctypes.CDLL(path)
+        P = ctypes.POINTER
+        sig = {
+            "bnx_create": ([P(vp), i32, u64, ctypes.c_char_p, vp], i32),
+            "bnx_destroy": ([vp], None),
+            "bnx_get_tune": ([vp, P(bnx_tune)], i32),
+            "bnx_set_tune": ([vp, P(bnx_tune)], i32),
+            "bnx_get_stats": ([vp, P(bnx_stats)], i32),
+            "bnx_prime_count": ([vp, P(u64)], i32),
+            "bnx_rad_segment": ([vp, u64, u64, vp, vp, vp], i32),
+            "bnx_search": ([vp, u64, u64, u32, P(bnx_pair), sz, P(sz)], i32),
+            "bnx_search_hash": ([vp, u64, u32, P(bnx_pair), sz, P(sz)], i32),
+            "bnx_batch": ([vp, P(bnx_interval), sz, P(bnx_pair), sz, P(sz), P(u64)], i32),
+            "bnx_server_start": ([vp, P(bnx_server_cfg)], i32),
+            "bnx_server_submit": ([vp, P(bnx_interval), P(u64)], i32),
+            "bnx_server_poll": ([vp, u64, P(bnx_pair), sz, P(sz), P(ctypes.c_double)], i32),
+            "bnx_server_stop": ([vp], i32),
+            "bnx_autotune": ([vp, P(bnx_interval), sz, i32, ctypes.c_char_p, sz], i32),
+            "bnx_strerror": ([i32], ctypes.c_char_p),
+            "bnx_last_error": ([], ctypes.c_char_p),
+        }
+        for name, (args, res) in sig.items():
+            f = getattr(L, name)
+            f.argtypes, f.restype = args, res
+        _lib = L
+        return L
+
+
+def _check(rc: int):
+    if rc != BNX_OK:
+        L = lib()
+        raise BnxError(rc, f"{L.bnx_strerror(rc).decode()}: {L.bnx_last_error().decode()}")
+
+
+def _pairs(buf, n):
+    return [(int(buf[i].m), int(buf[i].n), int(buf[i].kind)) for i in range(n)]
+
+
+# ---------------------------------------------------------------- ABI names --
+
+def bnx_strerror(code: int) -> str:
+    return lib().bnx_strerror(code).decode()
+
+
+def bnx_last_error() -> str:
+    return lib().bnx_last_error().decode()
+
+
+def bnx_create(device: int = 0, max_hi: int = 1 << 41, tune_json: str | None = None, stream: int | None = None):
+    h = vp()
+    _check(lib().bnx_create(ctypes.byref(h), device, max_hi,
+                            tune_json.encode() if tune_json else None, stream or None))
+    return h
+
+
+def bnx_destroy(ctx) -> None:
+    lib().bnx_destroy(ctx)
+
+
+def bnx_get_tune(ctx) -> bnx_tune:
+    t = bnx_tune()
+    _check(lib().bnx_get_tune(ctx, ctypes.byref(t)))
+    return t
+
+
+def bnx_set_tune(ctx, tune: bnx_tune) -> None:
+    _check(lib().bnx_set_tune(ctx, ctypes.byref(tune)))
+
+
+def bnx_get_stats(ctx) -> bnx_stats:
+    s = bnx_stats()
+    _check(lib().bnx_get_stats(ctx, ctypes.byref(s)))
+    return s
+
+
+def bnx_prime_count(ctx) -> int:
+    v = u64()
+    _check(lib().bnx_prime_count(ctx, ctypes.byref(v)))
+    return int(v.value)
+
+
+def bnx_rad_segment(ctx, lo: int, length: int, rad_out_ptr: int, sq_out_ptr: int | None = None,
+                    stream: int | None = None) -> None:
+    """Device pointers in, asynchronous on `stream`."""
+    _check(lib().bnx_rad_segment(ctx, lo, length, rad_out_ptr, sq_out_ptr or None, stream or None))
+
+
+def _grow_call(fn, cap=256):
+    while True:
+        buf = (bnx_pair * cap)()
+        n = sz()
+        rc = fn(buf, cap, ctypes.byref(n))
+        if rc == BNX_E_TRUNCATED:
+            cap = int(n.value) + 16
+            continue
+        _check(rc)
+        return buf, int(n.value)
+
+
+def bnx_search(ctx, lo: int, hi: int, kinds: int = 3):
+    """Pairs (m, n, kind) with lo <= n < hi, sorted by (n, m, kind)."""
+    buf, n = _grow_call(lambda b, c, pn: lib().bnx_search(ctx, lo, hi, kinds, b, c, pn))
+    return _pairs(buf, n)
+
+
+def bnx_search_hash(ctx, S: int, kinds: int = 3):
+    """Pairs (m, n, kind) with m < n < S by the device hash table."""
+    buf, n = _grow_call(lambda b, c, pn: lib().bnx_search_hash(ctx, S, kinds, b, c, pn))
+    return _pairs(buf, n)
+
+
+def make_intervals(intervals):
+    """Sequence of (lo, hi, kinds[, id]) or objects with .lo/.hi/.kinds -> ctypes array."""
+    arr = (bnx_interval * max(1, len(intervals)))()
+    for i, iv in enumerate(intervals):
+        if hasattr(iv, "lo"):
+            arr[i].lo, arr[i].hi, arr[i].kinds, arr[i].id = iv.lo, iv.hi, iv.kinds, getattr(iv, "id", i)
+        else:
+            arr[i].lo, arr[i].hi, arr[i].kinds = iv[0], iv[1], iv[2]
+            arr[i].id = iv[3] if len(iv) > 3 else i
+    return arr
+
+
+def bnx_batch(ctx, intervals, iv_array=None):
+    """All intervals in one pipeline.  Returns (pairs, offsets): pairs as
+    (interval index, m, n, kind) sorted by (interval, n, m, kind), offsets[i]..
+    offsets[i+1] delimiting interval i."""
+    k = len(intervals)
+    arr = iv_array if iv_array is not None else make_intervals(intervals)
+    offs = (u64 * (k + 1))()
+    buf, n = _grow_call(lambda b, c, pn: lib().bnx_batch(ctx, arr, k, b, c, pn, offs))
+    pairs = [(int(buf[i].iv), int(buf[i].m), int(buf[i].n), int(buf[i].kind)) for i in range(n)]
+    return pairs, [int(offs[i]) for i in range(k + 1)]
+
+
+def bnx_server_start(ctx, max_active: int = 64, slice_len: int = 1 << 28, mem_budget: int = 0) -> None:
+    cfg = bnx_server_cfg(max_active, 0, slice_len, mem_budget)
+    _check(lib().bnx_server_start(ctx, ctypes.byref(cfg)))
+
+
+def bnx_server_submit(ctx, lo: int, hi: int, kinds: int = 3, ident: int = 0) -> int:
+    iv = bnx_interval(lo, hi, kinds, ident)
+    t = u64()
+    _check(lib().bnx_server_submit(ctx, ctypes.byref(iv), ctypes.byref(t)))
+    return int(t.value)
+
+
+def bnx_server_poll(ctx, ticket: int):
+    """None while the request runs; else (pairs, latency_s)."""
+    cap = 64
+    while True:
+        buf = (bnx_pair * cap)()
+        n, lat = sz(), ctypes.c_double()
+        rc = lib().bnx_server_poll(ctx, ticket, buf, cap, ctypes.byref(n), ctypes.byref(lat))
+        if rc == BNX_E_BUSY:
+            return None
+        if rc == BNX_E_TRUNCATED:
+            cap = int(n.value) + 16
+            continue
+        _check(rc)
+        return _pairs(buf, int(n.value)), float(lat.value)
+
+
+def bnx_server_stop(ctx) -> None:
+    _check(lib().bnx_server_stop(ctx))
+
+
+def bnx_autotune(ctx, intervals, rounds: int = 2) -> str:
+    arr = make_intervals(intervals)
+    out = ctypes.create_string_buffer(512)
+    _check(lib().bnx_autotune(ctx, arr, len(intervals), rounds, out, 512))
+    return out.value.decode()
+
+
+class Context:
+    """Owns one bnx_ctx; the methods forward to the functions above."""
+
+    def __init__(self, device: int = 0, max_hi: int = 1 << 41, tune_json: str | None = None,
+                 stream: int | None = None):
+        self.h = bnx_create(device, max_hi, tune_json, stream)
+
+    def close(self):
+        if self.h:
+            bnx_destroy(self.h)
+            self.h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def search(self, lo, hi, kinds=3):
+        return bnx_search(self.h, lo, hi, kinds)
+
+    def search_hash(self, S, kinds=3):
+        return bnx_search_hash(self.h, S, kinds)
+
+    def batch(self, intervals):
+        return bnx_batch(self.h, intervals)
+
+    def rad_segment(self, lo, length, rad_ptr, sq_ptr=None, stream=None):
+        return bnx_rad_segment(self.h, lo, length, rad_ptr, sq_ptr, stream)
+
+    def stats(self):
+        return bnx_get_stats(self.h).as_dict()
+
+    def tune(self):
+        return bnx_get_tune(self.h).as_dict()
+
+    def set_tune(self, **kw):
+        t = bnx_get_tune(self.h)
+        for k, v in kw.items():
+            setattr(t, k, v)
+        bnx_set_tune(self.h, t)
+
+    def prime_count(self):
+        return bnx_prime_count(self.h)
+
+    def autotune(self, intervals, rounds=2):
+        return bnx_autotune(self.h, intervals, rounds)

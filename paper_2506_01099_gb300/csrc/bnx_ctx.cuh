@@ -1,0 +1,114 @@
+// The context object behind the opaque bnx_ctx handle (internal).
+#pragma once
+#include <atomic>
+#include <cstdint>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "benelux.h"
+#include "bnx_internal.cuh"
+
+namespace bnx {
+
+struct DevBuf {
+    void *p = nullptr;
+    size_t bytes = 0;
+};
+
+struct PlanTotals {
+    uint64_t segs, chunks, buckets, integers;
+};
+
+struct Server;  // server.cu
+
+struct SieveCfg {
+    bool valid = false;
+    int grid = 0, occ = 0;
+    uint32_t threads = 0, tile_log2 = 0, ctas = 0;
+    size_t smem = 0;
+};
+
+int fail(int code, const char *fmt, ...);
+int grow(DevBuf &b, size_t bytes);
+void release(DevBuf &b);
+
+#define CUDA_TRY(x)                                                                                         \
+    do {                                                                                                    \
+        cudaError_t e_ = (x);                                                                               \
+        if (e_ != cudaSuccess) {                                                                            \
+            cudaGetLastError();                                                                             \
+            return ::bnx::fail(BNX_E_CUDA, "%s: %s (%s:%d)", #x, cudaGetErrorString(e_), __FILE__, __LINE__); \
+        }                                                                                                   \
+    } while (0)
+
+}  // namespace bnx
+
+struct bnx_ctx {
+    int device = 0;
+    uint64_t max_hi = 0;
+    cudaStream_t stream = nullptr;
+    bool own_stream = false;
+    int n_sm = 0;
+    bnx_tune tune{};
+    uint32_t chunk_log2 = 26;
+
+    // device tables
+    bnx::DevBuf primes, spp, lpp, tmp_counts;
+    uint32_t np = 0, n_spp = 0, n_lpp = 0;
+    std::vector<uint64_t> lq;     // sorted large q (host copy)
+    std::vector<double> lq_inv;   // prefix sums of 1/q over lq
+
+    // workspace
+    bnx::DevBuf ivs, n_iv, ctr, bcnt, boff, bent, scan_tmp, surv, pairs, pairs_sorted, offsets;
+    bnx::DevBuf hkeys, hheads, hnext, hslot;
+    size_t surv_want = 1 << 16, pair_want = 1 << 12;
+    bnx::Counters *h_ctr = nullptr;  // pinned
+    bnx::IvDev *h_ivs = nullptr;     // pinned staging
+    size_t h_ivs_cap = 0;
+    uint32_t h_nk = 0;
+
+    // rad-mode outputs of the current call
+    uint64_t *rad_out = nullptr, *sq_out = nullptr;
+    uint64_t rad_lo = 0, rad_len = 0;
+    // hash-mode parameters of the current call
+    uint64_t hash_S = 0, hash_mask = 0;
+
+    // graph of the search pipeline
+    cudaGraphExec_t gexec = nullptr;
+    bool graph_valid = false;
+    bool capturing = false;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_s0 = nullptr, ev_s1 = nullptr;
+
+    bnx::SieveCfg sieve_cfg[3];
+    bnx_stats stats{};
+    std::mutex mu;
+    bnx::Server *server = nullptr;
+    std::atomic<bool> serving{false};
+
+    uint32_t seg_log2() const {
+        uint32_t l = 0;
+        while ((1u << l) < tune.seg_tiles) l++;
+        return tune.tile_log2 + l;
+    }
+    bool server_running() const { return serving.load(); }
+    std::vector<bnx::DevBuf *> all_bufs() {
+        return {&primes, &spp,   &lpp,          &tmp_counts, &ivs,  &n_iv,  &ctr,  &bcnt,  &boff,  &bent,
+                &scan_tmp, &surv, &pairs, &pairs_sorted, &offsets, &hkeys, &hheads, &hnext, &hslot};
+    }
+};
+
+namespace bnx {
+int build_pp_tables(bnx_ctx *c);
+uint64_t bucket_bound(const bnx_ctx *c, uint64_t lo, uint64_t hi, uint64_t nseg);
+int plan_host(bnx_ctx *c, const IvDev *iv, size_t k, PlanTotals *t);
+int ensure_ws(bnx_ctx *c, const PlanTotals &t, size_t k);
+Plan make_plan(const bnx_ctx *c);
+int sieve_config(bnx_ctx *c, int mode, int *grid, int *threads, size_t *smem);
+int record_pipeline(bnx_ctx *c, int mode, cudaStream_t s, bool timing);
+int run_search(bnx_ctx *c, size_t k, bool use_graph);
+int check_counters(bnx_ctx *c, bool *rerun);
+void fill_stats(bnx_ctx *c, uint64_t integers);
+int validate_interval(const bnx_ctx *c, uint64_t lo, uint64_t hi, uint32_t kinds);
+int search_staged(bnx_ctx *c, size_t k, bnx_pair *out, size_t cap, size_t *n_out, uint64_t *offsets);
+}  // namespace bnx

@@ -1,0 +1,137 @@
+// Internal declarations of libbenelux (not part of the ABI).
+//
+// Data layout in HBM (all device-resident for the life of a context):
+//   primes      u32[np]          every prime <= sqrt(max_hi), by a device sieve
+//   spp         SmallPP[n_spp]   odd prime powers q = p^k (k >= 2) with q <= Q:
+//                                struck inside the shared-memory tile
+//   lpp         LargePP[n_lpp]   odd prime powers q = p^k (k >= 2) with Q < q <= max_hi:
+//                                their hits go through the per-segment HBM buckets
+// Per pipeline run (workspace, grown on demand):
+//   ivs         IvDev[k]         the intervals with their segment and chunk bases
+//   bcnt/boff   u32/u64          bucket sizes and offsets per queue segment
+//   bent        uint2[]          bucket entries (value offset in segment, prime)
+//   surv        Survivor[]       n passing a necessary condition (compacted)
+//   pairs       PairDev[]        verified pairs, then sorted
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace bnx {
+
+constexpr int kMaxSpp = 256;    // in-tile prime powers per context
+constexpr int kMaxThreads = 1024;
+
+struct SmallPP {
+    uint32_t q;  // p^k
+    uint32_t p;
+};
+
+struct LargePP {
+    uint64_t q;  // p^k
+    uint32_t p;
+    uint32_t pad;
+};
+
+// One interval of a pipeline run.  n-range [lo, hi); sieved values [lo, hi].
+struct IvDev {
+    uint64_t lo, hi;
+    uint32_t kinds, id;
+    uint64_t seg_base;    // index of its first queue segment
+    uint64_t chunk_base;  // index of its first bucket-fill chunk
+};
+
+// Survivor of the per-kind necessary conditions (or a hash-search key).
+struct Survivor {
+    uint64_t n, a, b;  // a = rad(n), b = rad(n+1)
+    uint32_t kinds;    // bit 1: first-kind condition holds, bit 2: second-kind
+    uint32_t iv;
+};
+
+struct PairDev {
+    uint64_t m, n;
+    uint32_t kind, iv;
+};
+
+// Device counters of one run (zeroed at its start).
+struct Counters {
+    unsigned long long queue_head;   // next queue segment to pop
+    unsigned long long n_surv;       // survivors written (may exceed capacity)
+    unsigned long long n_pairs;      // pairs written (may exceed capacity)
+    unsigned long long bucket_hits;
+    unsigned long long surv1, surv2, candidates, hash_keys;
+    unsigned long long total_segs, total_chunks;  // plan totals
+    unsigned int err;                // nonzero: a device-side limit was hit
+    unsigned int pad;
+};
+
+// Error bits in Counters::err.
+constexpr unsigned kErrSurvOverflow = 1u;
+constexpr unsigned kErrPairOverflow = 2u;
+constexpr unsigned kErrBucketOverflow = 4u;
+constexpr unsigned kErrHashFull = 8u;
+
+// Everything a pipeline's kernels read.  Passed by value to every launch; the
+// sizes that vary per run live in device memory (Counters, IvDev) so that one
+// captured graph serves every batch that fits the workspace.
+struct Plan {
+    const IvDev *ivs;
+    const uint32_t *n_iv;  // device: number of intervals in this run
+    const SmallPP *spp;
+    uint32_t n_spp;
+    const LargePP *lpp;
+    uint32_t n_lpp;
+    uint32_t tile_log2, seg_log2;  // tile 2^tile_log2 integers, queue segment 2^seg_log2
+    uint32_t chunk_log2;           // bucket-fill chunk: 2^chunk_log2 sieved values
+    uint32_t *bcnt;                // [seg capacity]
+    unsigned long long *boff;      // [seg capacity + 1]
+    uint2 *bent;                   // [bucket capacity]
+    uint64_t seg_cap, bucket_cap;
+    Counters *ctr;
+    Survivor *surv;
+    uint64_t surv_cap;
+    PairDev *pairs;
+    PairDev *pairs_sorted;
+    uint64_t pair_cap;
+    uint64_t *iv_offsets;  // [k+1] pair offsets per interval
+    // rad mode
+    uint64_t *rad_out, *sq_out;
+    uint64_t rad_lo, rad_len;
+    // hash mode
+    uint64_t hash_S;
+    unsigned long long *hkeys;  // [hash slots], 0 = empty
+    uint32_t *hheads;           // [hash slots], 0xffffffff = empty chain
+    uint32_t *hnext;            // [surv cap]
+    uint32_t *hslot;            // [surv cap]
+    uint64_t hash_mask;
+};
+
+enum SieveMode { kModeSearch = 0, kModeRad = 1, kModeHash = 2 };
+
+// ---------------------------------------------------------------- kernels --
+// tables.cu
+void launch_prime_sieve(uint8_t *comp, uint64_t lim, cudaStream_t s);
+uint32_t flags_blocks(uint64_t n);
+void launch_scan_u8_count(const uint8_t *flags, uint64_t n, uint32_t *block_sums, uint32_t nblocks, cudaStream_t s);
+void launch_compact_primes(const uint8_t *comp, uint64_t lim, const uint32_t *block_offsets, uint32_t *primes,
+                           uint32_t nblocks, cudaStream_t s);
+void launch_exclusive_scan_u32(const uint32_t *in, unsigned long long *out, const unsigned long long *n_dev,
+                               uint64_t n_cap, unsigned long long *tmp, uint32_t tmp_cap, cudaStream_t s);
+void launch_build_pp(const uint32_t *primes, uint32_t np, uint64_t max_hi, uint32_t q_small, SmallPP *spp,
+                     uint32_t *n_spp, LargePP *lpp, uint32_t *n_lpp, uint64_t lpp_cap, cudaStream_t s);
+
+// sieve.cu
+void launch_plan(const Plan &P, uint32_t *n_iv_dev, IvDev *ivs, uint64_t max_iv, cudaStream_t s);
+void launch_bucket(const Plan &P, bool fill, int grid, cudaStream_t s);
+void launch_sieve(const Plan &P, int mode, int grid, int threads, size_t smem, cudaStream_t s);
+int sieve_occupancy(int mode, int threads, size_t smem, int *ctas_per_sm);
+size_t sieve_smem_bytes(uint32_t tile_log2);
+
+// verify.cu
+void launch_verify(const Plan &P, int grid, cudaStream_t s);
+void launch_sort(const Plan &P, int grid, cudaStream_t s);
+void launch_offsets(const Plan &P, int grid, cudaStream_t s);
+void launch_hash_insert(const Plan &P, int grid, cudaStream_t s);
+void launch_hash_pairs(const Plan &P, uint32_t kinds, int grid, cudaStream_t s);
+void launch_zero_counters(Counters *c, cudaStream_t s);
+
+}  // namespace bnx

@@ -1,0 +1,709 @@
+// Host side of libbenelux: contexts, device tables, workspace, the pipeline
+// (captured once as a CUDA graph and replayed), and the C ABI entry points
+// declared in include/benelux.h.
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "benelux.h"
+#include "bnx_ctx.cuh"
+
+namespace bnx {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+int grow(DevBuf &b, size_t bytes) {
+    if (bytes == 0) bytes = 16;
+    if (b.bytes >= bytes) return BNX_OK;
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+    if (cudaMalloc(&b.p, bytes) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BNX_E_NOMEM, "cudaMalloc of %zu bytes failed", bytes);
+    }
+    b.bytes = bytes;
+    return BNX_OK;
+}
+
+void release(DevBuf &b) {
+    if (b.p) cudaFree(b.p);
+    b.p = nullptr;
+    b.bytes = 0;
+}
+
+static uint64_t isqrt64(uint64_t x) {
+    uint64_t r = (uint64_t)std::sqrt((double)x);
+    while (r * r > x) r--;
+    while ((r + 1) * (r + 1) <= x) r++;
+    return r;
+}
+
+// ----------------------------------------------------------------- tune ----
+static void tune_defaults(bnx_tune *t) {
+    t->tile_log2 = 13;
+    t->seg_tiles = 8;
+    t->threads = 512;
+    t->ctas_per_sm = 0;
+    t->small_q_log2 = 14;
+}
+
+static int tune_check(const bnx_tune *t) {
+    if (t->tile_log2 < 10 || t->tile_log2 > 14) return fail(BNX_E_ARG, "tile_log2 must be in [10, 14]");
+    if (t->seg_tiles < 1 || t->seg_tiles > 64 || (t->seg_tiles & (t->seg_tiles - 1)))
+        return fail(BNX_E_ARG, "seg_tiles must be a power of two in [1, 64]");
+    if (t->threads != 128 && t->threads != 256 && t->threads != 512 && t->threads != 1024)
+        return fail(BNX_E_ARG, "threads must be 128, 256, 512 or 1024");
+    if (t->small_q_log2 < 8 || t->small_q_log2 > 20) return fail(BNX_E_ARG, "small_q_log2 must be in [8, 20]");
+    if (t->ctas_per_sm > 32) return fail(BNX_E_ARG, "ctas_per_sm must be <= 32");
+    return BNX_OK;
+}
+
+// Minimal reader for a flat JSON object of non-negative integers.
+static int parse_tune_json(const char *s, bnx_tune *t) {
+    struct F {
+        const char *name;
+        uint32_t *dst;
+    } fields[] = {{"tile_log2", &t->tile_log2},
+                  {"seg_tiles", &t->seg_tiles},
+                  {"threads", &t->threads},
+                  {"ctas_per_sm", &t->ctas_per_sm},
+                  {"small_q_log2", &t->small_q_log2}};
+    for (const F &f : fields) {
+        std::string key = std::string("\"") + f.name + "\"";
+        const char *p = strstr(s, key.c_str());
+        if (!p) continue;
+        p += key.size();
+        while (*p == ' ' || *p == '\t' || *p == '\n' || *p == '\r') p++;
+        if (*p != ':') return fail(BNX_E_ARG, "tune JSON: expected ':' after %s", f.name);
+        p++;
+        while (*p == ' ' || *p == '\t' || *p == '\n' || *p == '\r') p++;
+        if (*p < '0' || *p > '9') return fail(BNX_E_ARG, "tune JSON: %s is not a non-negative integer", f.name);
+        unsigned long v = strtoul(p, nullptr, 10);
+        *f.dst = (uint32_t)v;
+    }
+    return tune_check(t);
+}
+
+// ---------------------------------------------------------- tables --------
+int build_pp_tables(bnx_ctx *c) {
+    const uint32_t q_small = 1u << c->tune.small_q_log2;
+    const uint64_t lpp_cap = (uint64_t)c->np + 65536;
+    int rc;
+    if ((rc = grow(c->spp, sizeof(SmallPP) * kMaxSpp))) return rc;
+    if ((rc = grow(c->lpp, sizeof(LargePP) * lpp_cap))) return rc;
+    if ((rc = grow(c->tmp_counts, sizeof(uint32_t) * 4))) return rc;
+    uint32_t *cnt = (uint32_t *)c->tmp_counts.p;
+    launch_build_pp((uint32_t *)c->primes.p, c->np, c->max_hi, q_small, (SmallPP *)c->spp.p, cnt,
+                    (LargePP *)c->lpp.p, cnt + 1, lpp_cap, c->stream);
+    uint32_t h[2];
+    CUDA_TRY(cudaMemcpyAsync(h, cnt, sizeof h, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if (h[0] > (uint32_t)kMaxSpp)
+        return fail(BNX_E_ARG, "%u in-tile prime powers exceed the limit %d: lower small_q_log2", h[0], kMaxSpp);
+    if (h[1] > lpp_cap) return fail(BNX_E_NOMEM, "large prime-power table overflow");
+    c->n_spp = h[0];
+    c->n_lpp = h[1];
+    // host copy of the large q values, sorted, for the bucket capacity bound
+    std::vector<LargePP> tmp(c->n_lpp);
+    if (c->n_lpp)
+        CUDA_TRY(cudaMemcpy(tmp.data(), c->lpp.p, sizeof(LargePP) * c->n_lpp, cudaMemcpyDeviceToHost));
+    c->lq.resize(c->n_lpp);
+    for (uint32_t i = 0; i < c->n_lpp; i++) c->lq[i] = tmp[i].q;
+    std::sort(c->lq.begin(), c->lq.end());
+    c->lq_inv.assign(c->n_lpp + 1, 0.0);
+    for (uint32_t i = 0; i < c->n_lpp; i++) c->lq_inv[i + 1] = c->lq_inv[i] + 1.0 / (double)c->lq[i];
+    return BNX_OK;
+}
+
+static int build_tables(bnx_ctx *c) {
+    const uint64_t lim = std::max<uint64_t>(isqrt64(c->max_hi), 16);
+    DevBuf comp;
+    int rc;
+    if ((rc = grow(comp, lim + 1))) return rc;
+    CUDA_TRY(cudaMemsetAsync(comp.p, 0, lim + 1, c->stream));
+    launch_prime_sieve((uint8_t *)comp.p, lim, c->stream);
+    const uint32_t nb = flags_blocks(lim + 1);
+    DevBuf sums;
+    if ((rc = grow(sums, sizeof(uint32_t) * (nb + 1)))) {
+        release(comp);
+        return rc;
+    }
+    launch_scan_u8_count((uint8_t *)comp.p, lim + 1, (uint32_t *)sums.p, nb, c->stream);
+    uint32_t np = 0;
+    CUDA_TRY(cudaMemcpyAsync(&np, (uint32_t *)sums.p + nb, sizeof np, cudaMemcpyDeviceToHost, c->stream));
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    if ((rc = grow(c->primes, sizeof(uint32_t) * (np + 1)))) {
+        release(comp);
+        release(sums);
+        return rc;
+    }
+    launch_compact_primes((uint8_t *)comp.p, lim, (uint32_t *)sums.p, (uint32_t *)c->primes.p, nb, c->stream);
+    CUDA_TRY(cudaGetLastError());
+    CUDA_TRY(cudaStreamSynchronize(c->stream));
+    release(comp);
+    release(sums);
+    c->np = np;
+    return build_pp_tables(c);
+}
+
+// ------------------------------------------------------------ planning ----
+uint64_t bucket_bound(const bnx_ctx *c, uint64_t lo, uint64_t hi, uint64_t nseg) {
+    // hits of the large prime powers q <= hi among the W = hi - lo + 1 sieved
+    // values: sum floor(W/q) + 1 over q <= hi, plus the re-listing of a boundary
+    // value as the previous segment's halo (at most log_3(hi) < 28 prime powers
+    // divide it)
+    const uint64_t W = hi - lo + 1;
+    const size_t nq = std::upper_bound(c->lq.begin(), c->lq.end(), hi) - c->lq.begin();
+    const double h = c->lq_inv[nq];
+    return (uint64_t)std::ceil((double)W * h * (1.0 + 1e-9)) + nq + 28 * nseg + 16;
+}
+
+int plan_host(bnx_ctx *c, const IvDev *iv, size_t k, PlanTotals *t) {
+    const uint32_t seg_log2 = c->seg_log2(), chunk_log2 = c->chunk_log2;
+    t->segs = t->chunks = t->buckets = t->integers = 0;
+    for (size_t i = 0; i < k; i++) {
+        const uint64_t len = iv[i].hi - iv[i].lo;
+        const uint64_t ns = (len + (1ull << seg_log2) - 1) >> seg_log2;
+        t->segs += ns;
+        t->chunks += (len + 1 + (1ull << chunk_log2) - 1) >> chunk_log2;
+        t->buckets += bucket_bound(c, iv[i].lo, iv[i].hi, ns);
+        t->integers += len;
+    }
+    return BNX_OK;
+}
+
+int ensure_ws(bnx_ctx *c, const PlanTotals &t, size_t k) {
+    int rc;
+    bool changed = false;
+    auto need = [&](DevBuf &b, size_t bytes) -> int {
+        if (b.bytes >= bytes) return BNX_OK;
+        changed = true;
+        return grow(b, bytes + bytes / 4);
+    };
+    if ((rc = need(c->ivs, sizeof(IvDev) * (k + 1)))) return rc;
+    if ((rc = need(c->offsets, sizeof(uint64_t) * (k + 2)))) return rc;
+    if ((rc = need(c->bcnt, sizeof(uint32_t) * (t.segs + 1)))) return rc;
+    if ((rc = need(c->boff, sizeof(unsigned long long) * (t.segs + 2)))) return rc;
+    if ((rc = need(c->scan_tmp, sizeof(unsigned long long) * (t.segs / 4096 + 2)))) return rc;
+    if ((rc = need(c->bent, sizeof(uint2) * (t.buckets + 1)))) return rc;
+    if ((rc = need(c->surv, sizeof(Survivor) * c->surv_want))) return rc;
+    if ((rc = need(c->pairs, sizeof(PairDev) * c->pair_want))) return rc;
+    if ((rc = need(c->pairs_sorted, sizeof(PairDev) * c->pair_want))) return rc;
+    if (changed) c->graph_valid = false;
+    if (k + 1 > c->h_ivs_cap) {
+        if (c->h_ivs) cudaFreeHost(c->h_ivs);
+        c->h_ivs = nullptr;
+        c->h_ivs_cap = 0;
+        if (cudaMallocHost(&c->h_ivs, sizeof(IvDev) * (k + 1) * 2) != cudaSuccess) {
+            cudaGetLastError();
+            return fail(BNX_E_NOMEM, "pinned host allocation failed");
+        }
+        c->h_ivs_cap = (k + 1) * 2;
+    }
+    return BNX_OK;
+}
+
+Plan make_plan(const bnx_ctx *c) {
+    Plan P;
+    memset(&P, 0, sizeof P);
+    P.ivs = (const IvDev *)c->ivs.p;
+    P.n_iv = (const uint32_t *)c->n_iv.p;
+    P.spp = (const SmallPP *)c->spp.p;
+    P.n_spp = c->n_spp;
+    P.lpp = (const LargePP *)c->lpp.p;
+    P.n_lpp = c->n_lpp;
+    P.tile_log2 = c->tune.tile_log2;
+    P.seg_log2 = c->seg_log2();
+    P.chunk_log2 = c->chunk_log2;
+    P.bcnt = (uint32_t *)c->bcnt.p;
+    P.boff = (unsigned long long *)c->boff.p;
+    P.bent = (uint2 *)c->bent.p;
+    {
+        const uint64_t a = c->bcnt.bytes / sizeof(uint32_t), b = c->boff.bytes / sizeof(unsigned long long);
+        P.seg_cap = std::min(a > 0 ? a - 1 : 0, b > 1 ? b - 2 : 0);
+    }
+    P.bucket_cap = c->bent.bytes / sizeof(uint2);
+    P.ctr = (Counters *)c->ctr.p;
+    P.surv = (Survivor *)c->surv.p;
+    P.surv_cap = c->surv.bytes / sizeof(Survivor);
+    P.pairs = (PairDev *)c->pairs.p;
+    P.pairs_sorted = (PairDev *)c->pairs_sorted.p;
+    P.pair_cap = c->pairs.bytes / sizeof(PairDev);
+    P.iv_offsets = (uint64_t *)c->offsets.p;
+    P.rad_out = c->rad_out;
+    P.sq_out = c->sq_out;
+    P.rad_lo = c->rad_lo;
+    P.rad_len = c->rad_len;
+    P.hash_S = c->hash_S;
+    P.hkeys = (unsigned long long *)c->hkeys.p;
+    P.hheads = (uint32_t *)c->hheads.p;
+    P.hnext = (uint32_t *)c->hnext.p;
+    P.hslot = (uint32_t *)c->hslot.p;
+    P.hash_mask = c->hash_mask;
+    return P;
+}
+
+// Launch shape of the persistent sieve for the current tuning (queried outside
+// any stream capture and cached until the tuning changes).
+int sieve_config(bnx_ctx *c, int mode, int *grid, int *threads, size_t *smem) {
+    SieveCfg &sc = c->sieve_cfg[mode];
+    if (!sc.valid || sc.tile_log2 != c->tune.tile_log2 || sc.threads != c->tune.threads ||
+        sc.ctas != c->tune.ctas_per_sm) {
+        if (c->capturing) return fail(BNX_E_STATE, "sieve launch shape unknown during capture");
+        const int thr = (int)c->tune.threads;
+        const size_t smem_b = sieve_smem_bytes(c->tune.tile_log2);
+        int occ = 0;
+        int e = sieve_occupancy(mode, thr, smem_b, &occ);
+        if (e != 0) return fail(BNX_E_CUDA, "sieve occupancy query failed: %s", cudaGetErrorString((cudaError_t)e));
+        if (occ < 1) return fail(BNX_E_ARG, "sieve kernel does not fit an SM with this tuning");
+        const int per = c->tune.ctas_per_sm ? std::min<int>((int)c->tune.ctas_per_sm, occ) : occ;
+        sc.grid = c->n_sm * per;
+        sc.threads = c->tune.threads;
+        sc.smem = smem_b;
+        sc.tile_log2 = c->tune.tile_log2;
+        sc.ctas = c->tune.ctas_per_sm;
+        sc.occ = occ;
+        sc.valid = true;
+    }
+    *grid = sc.grid;
+    *threads = (int)sc.threads;
+    *smem = sc.smem;
+    return BNX_OK;
+}
+
+// Launch the whole pipeline on stream s (directly or under capture).
+int record_pipeline(bnx_ctx *c, int mode, cudaStream_t s, bool timing) {
+    Plan P = make_plan(c);
+    int sgrid, sthreads;
+    size_t ssmem;
+    int rc = sieve_config(c, mode, &sgrid, &sthreads, &ssmem);
+    if (rc) return rc;
+    const int bgrid = c->n_sm * 8;
+    CUDA_TRY(cudaMemsetAsync(c->ctr.p, 0, sizeof(Counters), s));
+    launch_plan(P, (uint32_t *)c->n_iv.p, (IvDev *)c->ivs.p, 0, s);
+    CUDA_TRY(cudaMemsetAsync(c->bcnt.p, 0, c->bcnt.bytes, s));
+    launch_bucket(P, false, bgrid, s);
+    launch_exclusive_scan_u32(P.bcnt, P.boff, &P.ctr->total_segs, P.seg_cap, (unsigned long long *)c->scan_tmp.p,
+                              (uint32_t)(c->scan_tmp.bytes / 8), s);
+    CUDA_TRY(cudaMemsetAsync(c->bcnt.p, 0, c->bcnt.bytes, s));
+    launch_bucket(P, true, bgrid, s);
+    if (timing) CUDA_TRY(cudaEventRecordWithFlags(c->ev_s0, s, c->capturing ? cudaEventRecordExternal : 0));
+    launch_sieve(P, mode, sgrid, sthreads, ssmem, s);
+    if (timing) CUDA_TRY(cudaEventRecordWithFlags(c->ev_s1, s, c->capturing ? cudaEventRecordExternal : 0));
+    if (mode == kModeSearch) {
+        launch_verify(P, c->n_sm * 4, s);
+        launch_sort(P, c->n_sm * 2, s);
+        launch_offsets(P, c->n_sm, s);
+    }
+    if (mode != kModeRad)
+        CUDA_TRY(cudaMemcpyAsync(c->h_ctr, c->ctr.p, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+    CUDA_TRY(cudaGetLastError());
+    return BNX_OK;
+}
+
+// Run the search pipeline for the intervals already in c->h_ivs[0..k), waiting
+// for completion; the counters land in c->h_ctr.
+int run_search(bnx_ctx *c, size_t k, bool use_graph) {
+    cudaStream_t s = c->stream;
+    CUDA_TRY(cudaMemcpyAsync(c->ivs.p, c->h_ivs, sizeof(IvDev) * k, cudaMemcpyHostToDevice, s));
+    c->h_nk = (uint32_t)k;
+    CUDA_TRY(cudaMemcpyAsync(c->n_iv.p, &c->h_nk, sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaEventRecord(c->ev0, s));
+    if (use_graph) {
+        if (!c->graph_valid) {
+            if (c->gexec) cudaGraphExecDestroy(c->gexec);
+            c->gexec = nullptr;
+            cudaGraph_t g;
+            int sg, st;
+            size_t ss;
+            int rc0 = sieve_config(c, kModeSearch, &sg, &st, &ss);
+            if (rc0) return rc0;
+            CUDA_TRY(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            c->capturing = true;
+            int rc = record_pipeline(c, kModeSearch, s, true);
+            c->capturing = false;
+            cudaError_t e = cudaStreamEndCapture(s, &g);
+            if (rc) {
+                if (e == cudaSuccess) cudaGraphDestroy(g);
+                return rc;
+            }
+            if (e != cudaSuccess) return fail(BNX_E_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
+            e = cudaGraphInstantiate(&c->gexec, g, 0);
+            cudaGraphDestroy(g);
+            if (e != cudaSuccess) return fail(BNX_E_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
+            c->graph_valid = true;
+        }
+        CUDA_TRY(cudaGraphLaunch(c->gexec, s));
+    } else {
+        int rc = record_pipeline(c, kModeSearch, s, true);
+        if (rc) return rc;
+    }
+    CUDA_TRY(cudaEventRecord(c->ev1, s));
+    CUDA_TRY(cudaStreamSynchronize(s));
+    return BNX_OK;
+}
+
+// Check the counters of a finished search; grow and ask for a rerun when a
+// device-side capacity was exceeded.  Returns BNX_OK, or BNX_E_OVERFLOW with
+// *rerun set when the run should be repeated.
+int check_counters(bnx_ctx *c, bool *rerun) {
+    *rerun = false;
+    const Counters &h = *c->h_ctr;
+    if (h.err & (kErrSurvOverflow | kErrPairOverflow)) {
+        if (h.n_surv > c->surv.bytes / sizeof(Survivor)) c->surv_want = (size_t)(h.n_surv + h.n_surv / 2 + 1024);
+        if (h.n_pairs > c->pairs.bytes / sizeof(PairDev)) c->pair_want = (size_t)(h.n_pairs + h.n_pairs / 2 + 1024);
+        *rerun = true;
+        return BNX_E_OVERFLOW;
+    }
+    if (h.err) return fail(BNX_E_OVERFLOW, "device capacity exceeded (flags 0x%x)", h.err);
+    return BNX_OK;
+}
+
+void fill_stats(bnx_ctx *c, uint64_t integers) {
+    const Counters &h = *c->h_ctr;
+    bnx_stats &st = c->stats;
+    memset(&st, 0, sizeof st);
+    st.integers = integers;
+    st.segments = h.total_segs;
+    st.bucket_hits = h.bucket_hits;
+    st.survivors1 = h.surv1;
+    st.survivors2 = h.surv2;
+    st.candidates = h.candidates;
+    st.pairs = h.n_pairs;
+    st.hash_keys = h.hash_keys;
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, c->ev0, c->ev1) == cudaSuccess) st.ms_total = ms;
+    if (cudaEventElapsedTime(&ms, c->ev_s0, c->ev_s1) == cudaSuccess) st.ms_sieve = ms;
+    cudaGetLastError();
+    st.sieve_launches = 1;
+}
+
+int validate_interval(const bnx_ctx *c, uint64_t lo, uint64_t hi, uint32_t kinds) {
+    if (lo < 1 || hi <= lo) return fail(BNX_E_ARG, "need 1 <= lo < hi (lo=%llu hi=%llu)", (unsigned long long)lo,
+                                        (unsigned long long)hi);
+    if (hi > c->max_hi) return fail(BNX_E_ARG, "hi=%llu exceeds max_hi=%llu", (unsigned long long)hi,
+                                    (unsigned long long)c->max_hi);
+    if (kinds < 1 || kinds > 3) return fail(BNX_E_ARG, "kinds must be 1, 2 or 3");
+    return BNX_OK;
+}
+
+// Search the intervals staged in c->h_ivs[0..k), retrying on capacity
+// overflow; copies the sorted pairs (and per-interval offsets) to the host.
+int search_staged(bnx_ctx *c, size_t k, bnx_pair *out, size_t cap, size_t *n_out, uint64_t *offsets) {
+    PlanTotals t;
+    plan_host(c, c->h_ivs, k, &t);
+    for (int attempt = 0; attempt < 4; attempt++) {
+        int rc = ensure_ws(c, t, k);
+        if (rc) return rc;
+        rc = run_search(c, k, true);
+        if (rc) return rc;
+        bool rerun = false;
+        rc = check_counters(c, &rerun);
+        if (rerun) continue;
+        if (rc) return rc;
+        fill_stats(c, t.integers);
+        const size_t np = (size_t)c->h_ctr->n_pairs;
+        if (n_out) *n_out = np;
+        const size_t ncopy = std::min(np, cap);
+        if (ncopy) {
+            if (!out) return fail(BNX_E_ARG, "out is NULL");
+            CUDA_TRY(cudaMemcpy(out, c->pairs_sorted.p, sizeof(PairDev) * ncopy, cudaMemcpyDeviceToHost));
+        }
+        if (offsets) CUDA_TRY(cudaMemcpy(offsets, c->offsets.p, sizeof(uint64_t) * (k + 1), cudaMemcpyDeviceToHost));
+        if (np > cap) return fail(BNX_E_TRUNCATED, "%zu pairs, buffer holds %zu", np, cap);
+        return BNX_OK;
+    }
+    return fail(BNX_E_OVERFLOW, "device capacities kept overflowing");
+}
+
+}  // namespace bnx
+
+using namespace bnx;
+
+// ======================================================================== ABI
+
+extern "C" {
+
+const char *bnx_strerror(int code) {
+    switch (code) {
+        case BNX_OK: return "ok";
+        case BNX_E_ARG: return "invalid argument";
+        case BNX_E_TRUNCATED: return "output truncated";
+        case BNX_E_NOMEM: return "out of memory";
+        case BNX_E_CUDA: return "CUDA error";
+        case BNX_E_TIMEOUT: return "timeout";
+        case BNX_E_BUSY: return "busy";
+        case BNX_E_STATE: return "invalid state";
+        case BNX_E_OVERFLOW: return "device capacity exceeded";
+        default: return "unknown error";
+    }
+}
+
+const char *bnx_last_error(void) { return g_last_error.c_str(); }
+
+int bnx_create(bnx_ctx **out, int device, uint64_t max_hi, const char *tune_json, void *stream) {
+    if (!out) return fail(BNX_E_ARG, "out is NULL");
+    *out = nullptr;
+    if (max_hi < 4 || max_hi > BNX_MAX_HI) return fail(BNX_E_ARG, "max_hi must be in [4, 2^42]");
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return fail(BNX_E_ARG, "no CUDA device %d", device);
+    }
+    bnx_ctx *c = new (std::nothrow) bnx_ctx();
+    if (!c) return fail(BNX_E_NOMEM, "host allocation failed");
+    c->device = device;
+    c->max_hi = max_hi;
+    tune_defaults(&c->tune);
+    int rc = BNX_OK;
+    if (tune_json && (rc = parse_tune_json(tune_json, &c->tune))) {
+        delete c;
+        return rc;
+    }
+    if (cudaSetDevice(device) != cudaSuccess) {
+        delete c;
+        return fail(BNX_E_CUDA, "cudaSetDevice(%d) failed", device);
+    }
+    cudaDeviceGetAttribute(&c->n_sm, cudaDevAttrMultiProcessorCount, device);
+    if (stream) {
+        c->stream = (cudaStream_t)stream;
+        c->own_stream = false;
+    } else {
+        if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+            delete c;
+            return fail(BNX_E_CUDA, "cudaStreamCreate failed");
+        }
+        c->own_stream = true;
+    }
+    if (cudaEventCreate(&c->ev0) || cudaEventCreate(&c->ev1) || cudaEventCreate(&c->ev_s0) ||
+        cudaEventCreate(&c->ev_s1) || cudaMallocHost(&c->h_ctr, sizeof(Counters))) {
+        cudaGetLastError();
+        bnx_destroy(c);
+        return fail(BNX_E_CUDA, "event or pinned allocation failed");
+    }
+    if ((rc = grow(c->ctr, sizeof(Counters))) || (rc = grow(c->n_iv, 16)) || (rc = build_tables(c))) {
+        bnx_destroy(c);
+        return rc;
+    }
+    *out = c;
+    return BNX_OK;
+}
+
+void bnx_destroy(bnx_ctx *c) {
+    if (!c) return;
+    bnx_server_stop(c);
+    cudaSetDevice(c->device);
+    if (c->stream) cudaStreamSynchronize(c->stream);
+    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    for (DevBuf *b : c->all_bufs()) release(*b);
+    if (c->h_ctr) cudaFreeHost(c->h_ctr);
+    if (c->h_ivs) cudaFreeHost(c->h_ivs);
+    if (c->ev0) cudaEventDestroy(c->ev0);
+    if (c->ev1) cudaEventDestroy(c->ev1);
+    if (c->ev_s0) cudaEventDestroy(c->ev_s0);
+    if (c->ev_s1) cudaEventDestroy(c->ev_s1);
+    if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+    cudaGetLastError();
+    delete c;
+}
+
+int bnx_get_tune(const bnx_ctx *c, bnx_tune *out) {
+    if (!c || !out) return fail(BNX_E_ARG, "NULL argument");
+    *out = c->tune;
+    return BNX_OK;
+}
+
+int bnx_set_tune(bnx_ctx *c, const bnx_tune *t) {
+    if (!c || !t) return fail(BNX_E_ARG, "NULL argument");
+    if (c->server_running()) return fail(BNX_E_STATE, "the serving loop owns the context");
+    int rc = tune_check(t);
+    if (rc) return rc;
+    std::lock_guard<std::mutex> g(c->mu);
+    cudaSetDevice(c->device);
+    const bool q_changed = t->small_q_log2 != c->tune.small_q_log2;
+    const bnx_tune old = c->tune;
+    c->tune = *t;
+    if (q_changed && (rc = build_pp_tables(c))) {
+        c->tune = old;
+        build_pp_tables(c);
+        return rc;
+    }
+    c->graph_valid = false;
+    return BNX_OK;
+}
+
+int bnx_get_stats(const bnx_ctx *c, bnx_stats *out) {
+    if (!c || !out) return fail(BNX_E_ARG, "NULL argument");
+    *out = c->stats;
+    return BNX_OK;
+}
+
+int bnx_prime_count(const bnx_ctx *c, uint64_t *out) {
+    if (!c || !out) return fail(BNX_E_ARG, "NULL argument");
+    *out = c->np;
+    return BNX_OK;
+}
+
+int bnx_rad_segment(bnx_ctx *c, uint64_t lo, uint64_t len, uint64_t *rad_out, uint64_t *sq_out, void *stream) {
+    if (!c || !rad_out) return fail(BNX_E_ARG, "NULL argument");
+    if (lo < 1 || len < 1 || len > (1ull << 31) || lo + len > c->max_hi)
+        return fail(BNX_E_ARG, "need 1 <= lo, 1 <= len <= 2^31, lo + len <= max_hi");
+    if (c->server_running()) return fail(BNX_E_STATE, "the serving loop owns the context");
+    std::lock_guard<std::mutex> g(c->mu);
+    cudaSetDevice(c->device);
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    IvDev iv;
+    memset(&iv, 0, sizeof iv);
+    iv.lo = lo;
+    iv.hi = lo + len;
+    iv.kinds = 3;
+    PlanTotals t;
+    plan_host(c, &iv, 1, &t);
+    int rc = ensure_ws(c, t, 1);
+    if (rc) return rc;
+    CUDA_TRY(cudaStreamSynchronize(s));  // the staging buffers below are reused across calls
+    c->h_ivs[0] = iv;
+    c->h_nk = 1;
+    CUDA_TRY(cudaMemcpyAsync(c->ivs.p, c->h_ivs, sizeof(IvDev), cudaMemcpyHostToDevice, s));
+    CUDA_TRY(cudaMemcpyAsync(c->n_iv.p, &c->h_nk, sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+    c->rad_out = rad_out;
+    c->sq_out = sq_out;
+    c->rad_lo = lo;
+    c->rad_len = len;
+    rc = record_pipeline(c, kModeRad, s, false);
+    c->rad_out = c->sq_out = nullptr;
+    return rc;
+}
+
+int bnx_search(bnx_ctx *c, uint64_t lo, uint64_t hi, uint32_t kinds, bnx_pair *out, size_t cap, size_t *n_out) {
+    if (!c) return fail(BNX_E_ARG, "NULL context");
+    int rc = validate_interval(c, lo, hi, kinds);
+    if (rc) return rc;
+    if (c->server_running()) return fail(BNX_E_STATE, "the serving loop owns the context");
+    std::lock_guard<std::mutex> g(c->mu);
+    cudaSetDevice(c->device);
+    PlanTotals t;
+    IvDev iv;
+    memset(&iv, 0, sizeof iv);
+    iv.lo = lo;
+    iv.hi = hi;
+    iv.kinds = kinds;
+    plan_host(c, &iv, 1, &t);
+    if ((rc = ensure_ws(c, t, 1))) return rc;
+    c->h_ivs[0] = iv;
+    return search_staged(c, 1, out, cap, n_out, nullptr);
+}
+
+int bnx_batch(bnx_ctx *c, const bnx_interval *ivs, size_t k, bnx_pair *out, size_t cap, size_t *n_out,
+              uint64_t *offsets) {
+    if (!c || (!ivs && k)) return fail(BNX_E_ARG, "NULL argument");
+    if (k == 0) {
+        if (n_out) *n_out = 0;
+        if (offsets) offsets[0] = 0;
+        return BNX_OK;
+    }
+    if (k > (1u << 24)) return fail(BNX_E_ARG, "at most 2^24 intervals per batch");
+    for (size_t i = 0; i < k; i++) {
+        int rc = validate_interval(c, ivs[i].lo, ivs[i].hi, ivs[i].kinds);
+        if (rc) return rc;
+    }
+    if (c->server_running()) return fail(BNX_E_STATE, "the serving loop owns the context");
+    std::lock_guard<std::mutex> g(c->mu);
+    cudaSetDevice(c->device);
+    PlanTotals t0;
+    t0.segs = t0.chunks = t0.buckets = 0;
+    int rc = ensure_ws(c, t0, k);
+    if (rc) return rc;
+    for (size_t i = 0; i < k; i++) {
+        IvDev &d = c->h_ivs[i];
+        memset(&d, 0, sizeof d);
+        d.lo = ivs[i].lo;
+        d.hi = ivs[i].hi;
+        d.kinds = ivs[i].kinds;
+        d.id = ivs[i].id;
+    }
+    return search_staged(c, k, out, cap, n_out, offsets);
+}
+
+int bnx_search_hash(bnx_ctx *c, uint64_t S, uint32_t kinds, bnx_pair *out, size_t cap, size_t *n_out) {
+    if (!c) return fail(BNX_E_ARG, "NULL context");
+    if (S < 2 || S > (1ull << 40) || S > c->max_hi) return fail(BNX_E_ARG, "need 2 <= S <= min(2^40, max_hi)");
+    if (kinds < 1 || kinds > 3) return fail(BNX_E_ARG, "kinds must be 1, 2 or 3");
+    if (c->server_running()) return fail(BNX_E_STATE, "the serving loop owns the context");
+    std::lock_guard<std::mutex> g(c->mu);
+    cudaSetDevice(c->device);
+    cudaStream_t s = c->stream;
+    IvDev iv;
+    memset(&iv, 0, sizeof iv);
+    iv.lo = 1;
+    iv.hi = S;
+    iv.kinds = 3;
+    PlanTotals t;
+    plan_host(c, &iv, 1, &t);
+    for (int attempt = 0; attempt < 4; attempt++) {
+        int rc = ensure_ws(c, t, 1);
+        if (rc) return rc;
+        c->h_ivs[0] = iv;
+        c->h_nk = 1;
+        CUDA_TRY(cudaMemcpyAsync(c->ivs.p, c->h_ivs, sizeof(IvDev), cudaMemcpyHostToDevice, s));
+        CUDA_TRY(cudaMemcpyAsync(c->n_iv.p, &c->h_nk, sizeof(uint32_t), cudaMemcpyHostToDevice, s));
+        c->hash_S = S;
+        CUDA_TRY(cudaEventRecord(c->ev0, s));
+        if ((rc = record_pipeline(c, kModeHash, s, true))) return rc;
+        CUDA_TRY(cudaStreamSynchronize(s));
+        if (c->h_ctr->err & kErrSurvOverflow) {
+            c->surv_want = (size_t)(c->h_ctr->n_surv + c->h_ctr->n_surv / 2 + 1024);
+            continue;
+        }
+        if (c->h_ctr->err) return fail(BNX_E_OVERFLOW, "device capacity exceeded (flags 0x%x)", c->h_ctr->err);
+        const uint64_t ns = c->h_ctr->n_surv;
+        uint64_t slots = 1024;
+        while (slots < 2 * ns) slots <<= 1;
+        if ((rc = grow(c->hkeys, slots * 8)) || (rc = grow(c->hheads, slots * 4)) ||
+            (rc = grow(c->hnext, (ns + 1) * 4)) || (rc = grow(c->hslot, (ns + 1) * 4)))
+            return rc;
+        c->hash_mask = slots - 1;
+        CUDA_TRY(cudaMemsetAsync(c->hkeys.p, 0, slots * 8, s));
+        CUDA_TRY(cudaMemsetAsync(c->hheads.p, 0xff, slots * 4, s));
+        Plan P = make_plan(c);
+        launch_hash_insert(P, c->n_sm * 4, s);
+        launch_hash_pairs(P, kinds, c->n_sm * 4, s);
+        launch_sort(P, c->n_sm * 2, s);
+        CUDA_TRY(cudaMemcpyAsync(c->h_ctr, c->ctr.p, sizeof(Counters), cudaMemcpyDeviceToHost, s));
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaEventRecord(c->ev1, s));
+        CUDA_TRY(cudaStreamSynchronize(s));
+        bool rerun = false;
+        rc = check_counters(c, &rerun);
+        if (rerun) continue;
+        if (rc) return rc;
+        fill_stats(c, t.integers);
+        const size_t np = (size_t)c->h_ctr->n_pairs;
+        if (n_out) *n_out = np;
+        const size_t ncopy = std::min(np, cap);
+        if (ncopy) {
+            if (!out) return fail(BNX_E_ARG, "out is NULL");
+            CUDA_TRY(cudaMemcpy(out, c->pairs_sorted.p, sizeof(PairDev) * ncopy, cudaMemcpyDeviceToHost));
+        }
+        if (np > cap) return fail(BNX_E_TRUNCATED, "%zu pairs, buffer holds %zu", np, cap);
+        return BNX_OK;
+    }
+    return fail(BNX_E_OVERFLOW, "device capacities kept overflowing");
+}
+
+}  // extern "C"

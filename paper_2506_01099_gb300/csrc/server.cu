@@ -1,0 +1,298 @@
+// Serving loop (continuous batching of interval requests) and the autotuner.
+//
+// Serving: a host thread owns the context while it runs.  Every iteration it
+//   1. admits waiting requests while a slot is free and the workspace their
+//      next slice needs fits the memory budget (free HBM by default);
+//   2. cuts the next slice of every active request and runs all slices as one
+//      batched pipeline (one persistent sieve launch over the shared queue), so
+//      the work of requests that arrived at different times overlaps on the GPU;
+//   3. appends each slice's pairs to its request and retires finished requests.
+// Results are exact, so a request's pairs are the same alone and in any mix.
+#include <algorithm>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <deque>
+#include <memory>
+#include <thread>
+#include <unordered_map>
+#include <vector>
+
+#include "benelux.h"
+#include "bnx_ctx.cuh"
+
+namespace bnx {
+
+using Clock = std::chrono::steady_clock;
+
+struct Request {
+    uint64_t ticket = 0;
+    bnx_interval iv{};
+    uint64_t cursor = 0;
+    std::vector<bnx_pair> pairs;
+    Clock::time_point t_submit, t_done;
+    bool done = false;
+    int status = BNX_OK;
+    uint64_t reserved = 0;
+};
+
+struct Server {
+    bnx_server_cfg cfg{};
+    uint64_t budget = 0, reserved = 0;
+    std::thread th;
+    std::mutex m;
+    std::condition_variable cv;
+    bool stop = false;
+    uint64_t next_ticket = 1;
+    std::deque<std::shared_ptr<Request>> pending;
+    std::vector<std::shared_ptr<Request>> active;
+    std::unordered_map<uint64_t, std::shared_ptr<Request>> all;
+    std::vector<bnx_pair> buf;
+    std::vector<uint64_t> offs;
+};
+
+// Device bytes one slice of a request needs in the shared workspace.
+static uint64_t slice_bytes(bnx_ctx *c, uint64_t lo, uint64_t hi) {
+    const uint64_t ns = ((hi - lo) >> c->seg_log2()) + 1;
+    return bucket_bound(c, lo, hi, ns) * sizeof(uint2) + ns * (sizeof(uint32_t) + sizeof(unsigned long long)) +
+           sizeof(IvDev) + 64;
+}
+
+static void serve(bnx_ctx *c) {
+    Server &S = *c->server;
+    cudaSetDevice(c->device);
+    for (;;) {
+        std::vector<std::shared_ptr<Request>> batch;
+        {
+            std::unique_lock<std::mutex> lk(S.m);
+            if (S.stop) break;
+            while (!S.pending.empty() && S.active.size() < S.cfg.max_active) {
+                auto r = S.pending.front();
+                const uint64_t hi = std::min(r->iv.hi, r->cursor + S.cfg.slice);
+                const uint64_t need = slice_bytes(c, r->cursor, hi);
+                if (S.reserved + need > S.budget && !S.active.empty()) break;  // wait for memory
+                r->reserved = need;
+                S.reserved += need;
+                S.active.push_back(r);
+                S.pending.pop_front();
+            }
+            if (S.active.empty()) {
+                S.cv.wait_for(lk, std::chrono::milliseconds(50));
+                continue;
+            }
+            batch = S.active;
+        }
+        const size_t k = batch.size();
+        PlanTotals t0{0, 0, 0, 0};
+        int rc = ensure_ws(c, t0, k);
+        if (rc == BNX_OK) {
+            for (size_t i = 0; i < k; i++) {
+                const Request &r = *batch[i];
+                IvDev &d = c->h_ivs[i];
+                memset(&d, 0, sizeof d);
+                d.lo = r.cursor;
+                d.hi = std::min(r.iv.hi, r.cursor + S.cfg.slice);
+                d.kinds = r.iv.kinds;
+                d.id = (uint32_t)i;
+            }
+            S.offs.assign(k + 1, 0);
+            size_t np = 0;
+            rc = search_staged(c, k, S.buf.data(), S.buf.size(), &np, S.offs.data());
+            if (rc == BNX_E_TRUNCATED) {
+                S.buf.resize(np + 64);
+                rc = search_staged(c, k, S.buf.data(), S.buf.size(), &np, S.offs.data());
+            }
+        }
+        std::lock_guard<std::mutex> lk(S.m);
+        std::vector<std::shared_ptr<Request>> still;
+        for (size_t i = 0; i < k; i++) {
+            Request &r = *batch[i];
+            if (rc == BNX_OK) {
+                for (uint64_t e = S.offs[i]; e < S.offs[i + 1]; e++) {
+                    bnx_pair p = S.buf[e];
+                    p.iv = r.iv.id;
+                    r.pairs.push_back(p);
+                }
+                r.cursor = std::min(r.iv.hi, r.cursor + S.cfg.slice);
+            } else {
+                r.status = rc;
+                r.cursor = r.iv.hi;
+            }
+            if (r.cursor >= r.iv.hi) {
+                r.done = true;
+                r.t_done = Clock::now();
+                S.reserved -= r.reserved;
+            } else {
+                still.push_back(batch[i]);
+            }
+        }
+        // requests admitted during this iteration are appended after `batch`
+        for (size_t i = k; i < S.active.size(); i++) still.push_back(S.active[i]);
+        S.active.swap(still);
+    }
+}
+
+}  // namespace bnx
+
+using namespace bnx;
+
+extern "C" {
+
+int bnx_server_start(bnx_ctx *c, const bnx_server_cfg *cfg) {
+    if (!c || !cfg) return fail(BNX_E_ARG, "NULL argument");
+    if (cfg->max_active < 1 || cfg->slice < 1) return fail(BNX_E_ARG, "max_active and slice must be >= 1");
+    std::lock_guard<std::mutex> g(c->mu);
+    if (c->serving.load()) return fail(BNX_E_STATE, "already serving");
+    cudaSetDevice(c->device);
+    Server *S = new (std::nothrow) Server();
+    if (!S) return fail(BNX_E_NOMEM, "host allocation failed");
+    S->cfg = *cfg;
+    if (cfg->mem_budget) {
+        S->budget = cfg->mem_budget;
+    } else {
+        size_t fr = 0, tot = 0;
+        if (cudaMemGetInfo(&fr, &tot) != cudaSuccess) {
+            cudaGetLastError();
+            delete S;
+            return fail(BNX_E_CUDA, "cudaMemGetInfo failed");
+        }
+        S->budget = (uint64_t)(0.9 * (double)fr);
+    }
+    S->buf.resize(4096);
+    c->server = S;
+    c->serving.store(true);
+    S->th = std::thread(serve, c);
+    return BNX_OK;
+}
+
+int bnx_server_submit(bnx_ctx *c, const bnx_interval *iv, uint64_t *ticket) {
+    if (!c || !iv || !ticket) return fail(BNX_E_ARG, "NULL argument");
+    if (!c->serving.load() || !c->server) return fail(BNX_E_STATE, "not serving");
+    int rc = validate_interval(c, iv->lo, iv->hi, iv->kinds);
+    if (rc) return rc;
+    Server &S = *c->server;
+    auto r = std::make_shared<Request>();
+    r->iv = *iv;
+    r->cursor = iv->lo;
+    r->t_submit = Clock::now();
+    {
+        std::lock_guard<std::mutex> lk(S.m);
+        r->ticket = S.next_ticket++;
+        S.pending.push_back(r);
+        S.all[r->ticket] = r;
+    }
+    S.cv.notify_one();
+    *ticket = r->ticket;
+    return BNX_OK;
+}
+
+int bnx_server_poll(bnx_ctx *c, uint64_t ticket, bnx_pair *out, size_t cap, size_t *n_out, double *latency_s) {
+    if (!c) return fail(BNX_E_ARG, "NULL context");
+    if (!c->server) return fail(BNX_E_STATE, "not serving");
+    Server &S = *c->server;
+    std::lock_guard<std::mutex> lk(S.m);
+    auto it = S.all.find(ticket);
+    if (it == S.all.end()) return fail(BNX_E_ARG, "unknown ticket %llu", (unsigned long long)ticket);
+    Request &r = *it->second;
+    if (!r.done) return BNX_E_BUSY;
+    if (r.status != BNX_OK) {
+        const int st = r.status;
+        S.all.erase(it);
+        return fail(st, "request failed: %s", bnx_strerror(st));
+    }
+    const size_t np = r.pairs.size();
+    if (n_out) *n_out = np;
+    if (latency_s) *latency_s = std::chrono::duration<double>(r.t_done - r.t_submit).count();
+    if (np > cap) return fail(BNX_E_TRUNCATED, "%zu pairs, buffer holds %zu", np, cap);
+    if (np && !out) return fail(BNX_E_ARG, "out is NULL");
+    if (np) memcpy(out, r.pairs.data(), np * sizeof(bnx_pair));
+    S.all.erase(it);
+    return BNX_OK;
+}
+
+int bnx_server_stop(bnx_ctx *c) {
+    if (!c) return fail(BNX_E_ARG, "NULL context");
+    Server *S = c->server;
+    if (!S) return BNX_OK;
+    {
+        std::lock_guard<std::mutex> lk(S->m);
+        S->stop = true;
+    }
+    S->cv.notify_all();
+    if (S->th.joinable()) S->th.join();
+    c->serving.store(false);
+    c->server = nullptr;
+    delete S;
+    return BNX_OK;
+}
+
+int bnx_autotune(bnx_ctx *c, const bnx_interval *iv, size_t k, int rounds, char *json_out, size_t json_cap) {
+    if (!c || !iv || k == 0) return fail(BNX_E_ARG, "need a context and at least one sample interval");
+    if (rounds < 1) rounds = 1;
+    bnx_tune best;
+    bnx_get_tune(c, &best);
+    std::vector<bnx_pair> buf(1024);
+    std::vector<uint64_t> offs(k + 1);
+    auto time_of = [&](const bnx_tune &t, float *ms) -> int {
+        int rc = bnx_set_tune(c, &t);
+        if (rc) return rc;
+        float bestms = 1e30f;
+        for (int r = 0; r < rounds + 1; r++) {  // the first run builds the graph
+            size_t np = 0;
+            rc = bnx_batch(c, iv, k, buf.data(), buf.size(), &np, offs.data());
+            if (rc == BNX_E_TRUNCATED) {
+                buf.resize(np + 64);
+                rc = bnx_batch(c, iv, k, buf.data(), buf.size(), &np, offs.data());
+            }
+            if (rc) return rc;
+            if (r > 0) bestms = std::min(bestms, c->stats.ms_total);
+        }
+        *ms = bestms;
+        return BNX_OK;
+    };
+    float best_ms = 0;
+    int rc = time_of(best, &best_ms);
+    if (rc) return rc;
+    const uint32_t tiles[] = {12, 13, 14};
+    const uint32_t segt[] = {1, 2, 4, 8, 16};
+    const uint32_t thr[] = {256, 512, 1024};
+    const uint32_t qs[] = {10, 12, 14, 16};
+    const uint32_t ctas[] = {0, 1, 2};
+    for (int pass = 0; pass < 2; pass++) {
+        for (int field = 0; field < 5; field++) {
+            const uint32_t *vals;
+            int nv;
+            switch (field) {
+                case 0: vals = tiles; nv = 3; break;
+                case 1: vals = segt; nv = 5; break;
+                case 2: vals = thr; nv = 3; break;
+                case 3: vals = qs; nv = 4; break;
+                default: vals = ctas; nv = 3; break;
+            }
+            for (int v = 0; v < nv; v++) {
+                bnx_tune t = best;
+                uint32_t *f = field == 0 ? &t.tile_log2 : field == 1 ? &t.seg_tiles : field == 2 ? &t.threads
+                                                      : field == 3 ? &t.small_q_log2 : &t.ctas_per_sm;
+                if (*f == vals[v]) continue;
+                *f = vals[v];
+                float ms = 0;
+                if (time_of(t, &ms) != BNX_OK) continue;  // a tuning that does not fit is skipped
+                if (ms < best_ms) {
+                    best_ms = ms;
+                    best = t;
+                }
+            }
+        }
+    }
+    rc = bnx_set_tune(c, &best);
+    if (rc) return rc;
+    if (json_out && json_cap) {
+        snprintf(json_out, json_cap,
+                 "{\"tile_log2\": %u, \"seg_tiles\": %u, \"threads\": %u, \"ctas_per_sm\": %u, "
+                 "\"small_q_log2\": %u, \"ms\": %.4f}",
+                 best.tile_log2, best.seg_tiles, best.threads, best.ctas_per_sm, best.small_q_log2, best_ms);
+    }
+    return BNX_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,428 @@
+// Planning, large-prime bucket fill and the shared-memory tile sieve.
+//
+// The n-range [lo, hi) of every interval is cut into queue segments of
+// L_seg = 2^seg_log2 integers; a segment sieves the values [seg_lo, seg_lo+len]
+// (len n values plus the one-integer halo that rad(n+1) of its last n needs --
+// the overlap of consecutive chunks in Sec. 2.2).
+//
+// Per value x the tile holds s(x) = x_odd / rad(x_odd), the product of p^(e-1)
+// over the odd prime powers p^e || x (the "square part"; rad(x) = x / s(x) up to
+// the power of 2, which comes from counting trailing zeros as in Sec. 3.1).  It
+// is Algorithm 1 (Sec. 2.1) restated multiplicatively: where Algorithm 1 divides
+// r[x] by p at every multiple of p^k (k >= 2), the tile multiplies s[x] by p.
+//   - prime powers q = p^k <= Q: struck inside the shared-memory tile, 32 lanes
+//     of a warp on 32 consecutive multiples of one q (Sec. 3.1: once the first
+//     multiple is known all strikes of a prime power are independent);
+//   - prime powers q > Q: a bucket-fill pass lists each hit (value offset in its
+//     segment, p) in the segment's HBM bucket; the tile applies them.
+// Strikes of different prime powers may meet at one x, so every strike is a
+// 64-bit shared-memory compare-and-swap multiply.
+//
+// The per-n filter uses exact necessary conditions (derived from the Chinese
+// remainder theorem; a = rad(n), b = rad(n+1), coprime):
+//   first kind : ab | n - m   ->  ab <= n - 1
+//   second kind: ab | m+n+1   ->  some multiple of ab lies in [n+2, 2n]
+// In terms of the square parts, ab = n(n+1) / (s(n) s(n+1)), so ab <= 2n iff
+// s(n)s(n+1) >= (n+1)/2 (s including the power of 2).  A bit-length bound on
+// s(n)s(n+1) rejects almost every n with a few integer instructions; the rare
+// rest is decided exactly (64-bit divisions and 128-bit products).
+#include "bnx_internal.cuh"
+
+namespace bnx {
+
+namespace {
+
+__device__ __forceinline__ uint32_t ctz64(uint64_t x) { return (uint32_t)(__ffsll((long long)x) - 1); }
+__device__ __forceinline__ uint32_t bitlen64(uint64_t x) { return 64u - (uint32_t)__clzll((long long)x); }
+__device__ __forceinline__ uint32_t flog2_64(uint64_t x) { return 63u - (uint32_t)__clzll((long long)x); }
+
+// s[x] *= p, atomically (strikes of different prime powers may meet at x)
+__device__ __forceinline__ void smul(unsigned long long *a, unsigned long long p) {
+    unsigned long long old = *a, assumed;
+    do {
+        assumed = old;
+        old = atomicCAS(a, assumed, assumed * p);
+    } while (old != assumed);
+}
+
+// index of the interval owning item `x`: the last v with base(v) <= x
+template <bool SEG>
+__device__ __forceinline__ uint32_t find_iv(const IvDev *ivs, uint32_t k, uint64_t x) {
+    uint32_t lo = 0, hi = k;  // invariant: answer in [lo, hi)
+    while (hi - lo > 1) {
+        uint32_t mid = (lo + hi) >> 1;
+        uint64_t b = SEG ? ivs[mid].seg_base : ivs[mid].chunk_base;
+        if (b <= x) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+// ---------------------------------------------------------------- plan ----
+// One block: per interval the number of queue segments (ceil((hi-lo)/L_seg))
+// and of bucket-fill chunks (ceil((hi-lo+1)/2^chunk_log2)), exclusive scans of
+// both, and the totals.
+__global__ void k_plan(IvDev *ivs, const uint32_t *n_iv_dev, uint32_t seg_log2, uint32_t chunk_log2,
+                       Counters *ctr) {
+    __shared__ unsigned long long sbuf[1024], cbuf[1024];
+    __shared__ unsigned long long scarry, ccarry;
+    uint32_t k = *n_iv_dev;
+    if (threadIdx.x == 0) scarry = ccarry = 0;
+    __syncthreads();
+    for (uint32_t base = 0; base < k; base += blockDim.x) {
+        uint32_t i = base + threadIdx.x;
+        unsigned long long ns = 0, nc = 0;
+        if (i < k) {
+            uint64_t len = ivs[i].hi - ivs[i].lo;
+            ns = (len + (1ull << seg_log2) - 1) >> seg_log2;
+            nc = (len + 1 + (1ull << chunk_log2) - 1) >> chunk_log2;
+        }
+        sbuf[threadIdx.x] = ns;
+        cbuf[threadIdx.x] = nc;
+        __syncthreads();
+        for (uint32_t o = 1; o < blockDim.x; o <<= 1) {
+            unsigned long long ts = threadIdx.x >= o ? sbuf[threadIdx.x - o] : 0;
+            unsigned long long tc = threadIdx.x >= o ? cbuf[threadIdx.x - o] : 0;
+            __syncthreads();
+            sbuf[threadIdx.x] += ts;
+            cbuf[threadIdx.x] += tc;
+            __syncthreads();
+        }
+        if (i < k) {
+            ivs[i].seg_base = scarry + sbuf[threadIdx.x] - ns;
+            ivs[i].chunk_base = ccarry + cbuf[threadIdx.x] - nc;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            scarry += sbuf[blockDim.x - 1];
+            ccarry += cbuf[blockDim.x - 1];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x == 0) {
+        ctr->total_segs = scarry;
+        ctr->total_chunks = ccarry;
+    }
+}
+
+// ------------------------------------------------------------- buckets ----
+// Work unit: (chunk of sieved values of one interval, large prime power q).
+// Blocks stride over chunks; the threads of a block stride over the table.
+// Every multiple y of q in the chunk is a hit of its segment at offset y-seg_lo;
+// a multiple on a segment boundary is also the previous segment's halo value.
+template <bool FILL>
+__global__ void __launch_bounds__(256) k_bucket(Plan P) {
+    __shared__ uint32_t s_iv;
+    const uint64_t total_chunks = P.ctr->total_chunks;
+    const uint32_t k = *P.n_iv;
+    const uint64_t lseg = 1ull << P.seg_log2;
+    if (FILL && blockIdx.x == 0 && threadIdx.x == 0) P.ctr->bucket_hits = P.boff[P.ctr->total_segs];
+    for (uint64_t c = blockIdx.x; c < total_chunks; c += gridDim.x) {
+        if (threadIdx.x == 0) s_iv = find_iv<false>(P.ivs, k, c);
+        __syncthreads();
+        const IvDev iv = P.ivs[s_iv];
+        const uint64_t c_in = c - iv.chunk_base;
+        const uint64_t v0 = iv.lo + (c_in << P.chunk_log2);
+        uint64_t v1 = v0 + (1ull << P.chunk_log2) - 1;
+        if (v1 > iv.hi) v1 = iv.hi;
+        const uint64_t nseg = (iv.hi - iv.lo + lseg - 1) >> P.seg_log2;
+        for (uint32_t j = threadIdx.x; j < P.n_lpp; j += blockDim.x) {
+            const uint64_t q = P.lpp[j].q;
+            if (q > v1) continue;
+            const uint32_t p = P.lpp[j].p;
+            const uint64_t r = v0 % q;
+            for (uint64_t y = r ? v0 + (q - r) : v0; y <= v1; y += q) {
+                const uint64_t d = y - iv.lo;
+                const uint64_t s = d >> P.seg_log2;
+                const uint32_t o = (uint32_t)(d & (lseg - 1));
+#pragma unroll
+                for (int rep = 0; rep < 2; rep++) {
+                    uint64_t seg;
+                    uint32_t off;
+                    if (rep == 0) {
+                        if (s >= nseg) continue;
+                        seg = iv.seg_base + s;
+                        off = o;
+                    } else {
+                        if (o != 0 || s == 0) continue;
+                        seg = iv.seg_base + s - 1;  // halo of the previous segment
+                        off = (uint32_t)lseg;
+                    }
+                    if (seg >= P.seg_cap) {
+                        atomicOr(&P.ctr->err, kErrBucketOverflow);
+                        continue;
+                    }
+                    if (!FILL) {
+                        atomicAdd(&P.bcnt[seg], 1u);
+                    } else {
+                        const uint32_t pos = atomicAdd(&P.bcnt[seg], 1u);
+                        const unsigned long long at = P.boff[seg] + pos;
+                        if (at < P.boff[seg + 1] && at < P.bucket_cap) P.bent[at] = make_uint2(off, p);
+                        else atomicOr(&P.ctr->err, kErrBucketOverflow);
+                    }
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+// --------------------------------------------------------------- sieve ----
+// Shared memory: the tile, then per in-tile prime power q, p, the offset of its
+// first multiple in the current tile, L_tile mod q, its hit count and
+// warp-chunk prefix, and the list of warp-chunks of the current tile.
+constexpr int kMaxChunks = 1024;
+
+struct SmemLayout {
+    size_t tile_bytes;
+    size_t total;
+};
+
+__host__ __device__ inline SmemLayout smem_layout(uint32_t tile_log2) {
+    SmemLayout L;
+    L.tile_bytes = (((size_t)1 << tile_log2) + 2) * sizeof(unsigned long long);
+    L.tile_bytes = (L.tile_bytes + 15) & ~(size_t)15;
+    L.total = L.tile_bytes + (size_t)6 * kMaxSpp * sizeof(uint32_t) + sizeof(uint32_t) * (kMaxSpp + 1) +
+              sizeof(uint32_t) * kMaxChunks;
+    return L;
+}
+
+// exact decision for one n whose bit-length bound did not reject it
+// s0, s1: odd square parts of n and n+1 (from the tile)
+__device__ __noinline__ uint32_t exact_kinds(uint64_t n, uint64_t s0, uint64_t s1, uint32_t kinds, int mode,
+                                             uint64_t hash_S, uint64_t *pa, uint64_t *pb) {
+    const uint32_t t0 = ctz64(n), t1 = ctz64(n + 1);
+    const uint64_t sn = s0 << (t0 ? t0 - 1 : 0);
+    const uint64_t sn1 = s1 << (t1 ? t1 - 1 : 0);
+    const uint64_t a = n / sn, b = (n + 1) / sn1;
+    *pa = a;
+    *pb = b;
+    const unsigned __int128 ab = (unsigned __int128)a * b;
+    if (mode == kModeHash) return ab <= (unsigned __int128)2 * hash_S ? 3u : 0u;
+    uint32_t r = 0;
+    if ((kinds & 1) && ab <= (unsigned __int128)(n - 1)) r |= 1;
+    if ((kinds & 2) && ab <= (unsigned __int128)2 * n) {
+        const uint64_t abl = (uint64_t)ab;
+        const uint64_t jlo = (n + 2 + abl - 1) / abl, jhi = (2 * n) / abl;
+        if (jlo <= jhi) r |= 2;
+    }
+    return r;
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(1024) k_sieve(Plan P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const uint32_t tile_log2 = P.tile_log2;
+    const uint32_t LT = 1u << tile_log2;
+    const SmemLayout lay = smem_layout(tile_log2);
+    unsigned long long *tile = reinterpret_cast<unsigned long long *>(smem_raw);
+    uint32_t *sq = reinterpret_cast<uint32_t *>(smem_raw + lay.tile_bytes);
+    uint32_t *sp = sq + kMaxSpp;
+    uint32_t *soff = sp + kMaxSpp;
+    uint32_t *slmod = soff + kMaxSpp;
+    uint32_t *scnt = slmod + kMaxSpp;
+    uint32_t *sc = scnt + kMaxSpp;      // warp-chunks per prime power (scratch)
+    uint32_t *spre = sc + kMaxSpp;      // kMaxSpp + 1
+    uint32_t *schunks = spre + kMaxSpp + 1;
+    __shared__ unsigned long long s_seg;
+    __shared__ uint32_t s_iv, s_nchunks;
+
+    const uint32_t tid = threadIdx.x, NT = blockDim.x;
+    const uint32_t lane = tid & 31, warp = tid >> 5, nwarps = NT >> 5;
+    const uint32_t nspp = P.n_spp;
+    const uint32_t k = *P.n_iv;
+    const unsigned long long total_segs = P.ctr->total_segs;
+
+    for (uint32_t j = tid; j < nspp; j += NT) {
+        const SmallPP e = P.spp[j];
+        sq[j] = e.q;
+        sp[j] = e.p;
+        slmod[j] = LT % e.q;
+    }
+
+    for (;;) {
+        __syncthreads();  // previous segment fully done (tile, tables)
+        if (tid == 0) {
+            s_seg = atomicAdd(&P.ctr->queue_head, 1ull);
+            s_iv = s_seg < total_segs ? find_iv<true>(P.ivs, k, s_seg) : 0;
+        }
+        __syncthreads();
+        const unsigned long long seg = s_seg;
+        if (seg >= total_segs) break;
+        const IvDev iv = P.ivs[s_iv];
+        const uint64_t seg_lo = iv.lo + ((seg - iv.seg_base) << P.seg_log2);
+        const uint64_t rem = iv.hi - seg_lo;
+        const uint32_t seg_len = rem < (1ull << P.seg_log2) ? (uint32_t)rem : (1u << P.seg_log2);
+        const unsigned long long b0 = P.boff[seg], b1 = P.boff[seg + 1];
+
+        for (uint32_t j = tid; j < nspp; j += NT) {
+            const uint32_t q = sq[j];
+            const uint32_t r = (uint32_t)(seg_lo % q);
+            soff[j] = r ? q - r : 0;
+        }
+
+        for (uint32_t t0 = 0; t0 < seg_len; t0 += LT) {
+            // tile: n in [t_lo, t_lo + tl), values t_lo .. t_lo + tl (halo)
+            const uint32_t tl = (seg_len - t0) < LT ? (seg_len - t0) : LT;
+            const uint64_t t_lo = seg_lo + t0;
+            __syncthreads();  // offsets written, previous tile's epilogue done
+            for (uint32_t i = tid; i <= tl; i += NT) tile[i] = 1ull;
+            for (uint32_t j = tid; j < nspp; j += NT) {
+                const uint32_t off = soff[j];
+                const uint32_t cnt = off <= tl ? (tl - off) / sq[j] + 1 : 0;
+                scnt[j] = cnt;
+                sc[j] = (cnt + 31) >> 5;
+            }
+            __syncthreads();
+            if (warp == 0) {
+                // exclusive scan of the warp-chunk counts, then the chunk list
+                constexpr int kPer = kMaxSpp / 32;
+                uint32_t v[kPer];
+                uint32_t sum = 0;
+#pragma unroll
+                for (int u = 0; u < kPer; u++) {
+                    const uint32_t j = lane * kPer + u;
+                    v[u] = j < nspp ? sc[j] : 0;
+                    sum += v[u];
+                }
+                uint32_t inc = sum;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const uint32_t x = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= (uint32_t)o) inc += x;
+                }
+                uint32_t run = inc - sum;
+#pragma unroll
+                for (int u = 0; u < kPer; u++) {
+                    const uint32_t j = lane * kPer + u;
+                    if (j < nspp) {
+                        spre[j] = run;
+                        for (uint32_t c = 0; c < v[u]; c++)
+                            if (run + c < kMaxChunks) schunks[run + c] = j | (c << 8);
+                    }
+                    run += v[u];
+                }
+                if (lane == 31) s_nchunks = inc < kMaxChunks ? inc : kMaxChunks;
+            }
+            __syncthreads();
+            // small prime powers: one warp-chunk = 32 consecutive multiples of q
+            const uint32_t nch = s_nchunks;
+            for (uint32_t g = warp; g < nch; g += nwarps) {
+                const uint32_t e = schunks[g];
+                const uint32_t j = e & 255u;
+                const uint32_t i = ((e >> 8) << 5) + lane;
+                if (i < scnt[j]) smul(&tile[soff[j] + i * sq[j]], sp[j]);
+            }
+            // large prime powers from this segment's bucket
+            for (unsigned long long e = b0 + tid; e < b1; e += NT) {
+                const uint2 h = P.bent[e];
+                if (h.x >= t0 && h.x <= t0 + tl) smul(&tile[h.x - t0], h.y);
+            }
+            __syncthreads();
+            // offsets of the next tile: (off - L_tile) mod q
+            for (uint32_t j = tid; j < nspp; j += NT) {
+                const uint32_t off = soff[j], lm = slmod[j];
+                soff[j] = off >= lm ? off - lm : off + sq[j] - lm;
+            }
+
+            if (MODE == kModeRad) {
+                for (uint32_t i = tid; i < tl; i += NT) {
+                    const uint64_t x = t_lo + i;
+                    const uint64_t gi = x - P.rad_lo;
+                    if (gi < P.rad_len) {
+                        const uint32_t tz = ctz64(x);
+                        const uint64_t s = tile[i] << (tz ? tz - 1 : 0);
+                        P.rad_out[gi] = x / s;
+                        if (P.sq_out) P.sq_out[gi] = s;
+                    }
+                }
+            } else {
+                // bit-length bound: s(n)s(n+1) < 2^bits with s including the 2-part
+                int thr;
+                if (MODE == kModeSearch) {
+                    thr = (int)flog2_64(t_lo + 1);  // reject when 2^(bits+1) <= n+1
+                } else {
+                    const uint64_t S2 = 2 * P.hash_S;
+                    const int clog = (int)flog2_64(S2) + ((S2 & (S2 - 1)) ? 1 : 0);
+                    thr = (int)flog2_64(t_lo) + (int)flog2_64(t_lo + 1) - clog;  // reject when bits <= thr
+                }
+                const uint32_t kinds = iv.kinds;
+                for (uint32_t base = 0; base < tl; base += NT) {
+                    const uint32_t i = base + tid;
+                    bool cand = false;
+                    uint64_t n = 0, s0 = 0, s1 = 0;
+                    if (i < tl) {
+                        s0 = tile[i];
+                        s1 = tile[i + 1];
+                        n = t_lo + i;
+                        const int bits = (int)(bitlen64(s0) + bitlen64(s1) + ctz64(n + (n & 1)) - 1);
+                        cand = MODE == kModeSearch ? (bits + 1 > thr) : (bits > thr);
+                    }
+                    if (__any_sync(0xffffffffu, cand)) {
+                        uint32_t kk = 0;
+                        uint64_t a = 0, b = 0;
+                        if (cand) kk = exact_kinds(n, s0, s1, kinds, MODE, P.hash_S, &a, &b);
+                        const uint32_t m = __ballot_sync(0xffffffffu, kk != 0);
+                        if (m) {
+                            unsigned long long wbase = 0;
+                            if (lane == 0) wbase = atomicAdd(&P.ctr->n_surv, (unsigned long long)__popc(m));
+                            wbase = __shfl_sync(0xffffffffu, wbase, 0);
+                            if (kk) {
+                                const unsigned long long at = wbase + __popc(m & ((1u << lane) - 1));
+                                if (at < P.surv_cap) {
+                                    Survivor sv;
+                                    sv.n = n;
+                                    sv.a = a;
+                                    sv.b = b;
+                                    sv.kinds = kk;
+                                    sv.iv = s_iv;
+                                    P.surv[at] = sv;
+                                } else {
+                                    atomicOr(&P.ctr->err, kErrSurvOverflow);
+                                }
+                                if (MODE == kModeSearch) {
+                                    if (kk & 1) atomicAdd(&P.ctr->surv1, 1ull);
+                                    if (kk & 2) atomicAdd(&P.ctr->surv2, 1ull);
+                                }
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+
+size_t sieve_smem_bytes(uint32_t tile_log2) { return smem_layout(tile_log2).total; }
+
+void launch_plan(const Plan &P, uint32_t *n_iv_dev, IvDev *ivs, uint64_t max_iv, cudaStream_t s) {
+    (void)max_iv;
+    k_plan<<<1, 1024, 0, s>>>(ivs, n_iv_dev, P.seg_log2, P.chunk_log2, P.ctr);
+}
+
+void launch_bucket(const Plan &P, bool fill, int grid, cudaStream_t s) {
+    if (fill) k_bucket<true><<<grid, 256, 0, s>>>(P);
+    else k_bucket<false><<<grid, 256, 0, s>>>(P);
+}
+
+static const void *sieve_fn(int mode) {
+    if (mode == kModeRad) return (const void *)k_sieve<kModeRad>;
+    if (mode == kModeHash) return (const void *)k_sieve<kModeHash>;
+    return (const void *)k_sieve<kModeSearch>;
+}
+
+int sieve_occupancy(int mode, int threads, size_t smem, int *ctas_per_sm) {
+    const void *fn = sieve_fn(mode);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, fn, threads, smem);
+}
+
+void launch_sieve(const Plan &P, int mode, int grid, int threads, size_t smem, cudaStream_t s) {
+    if (mode == kModeRad) k_sieve<kModeRad><<<grid, threads, smem, s>>>(P);
+    else if (mode == kModeHash) k_sieve<kModeHash><<<grid, threads, smem, s>>>(P);
+    else k_sieve<kModeSearch><<<grid, threads, smem, s>>>(P);
+}
+
+}  // namespace bnx

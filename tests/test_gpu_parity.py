@@ -1,0 +1,224 @@
+"""CUDA path vs the oracle, element by element, through the C ABI (GPU only).
+
+Radicals are compared bit-exactly on segments that span several tiles and
+queue segments with a ragged tail; pair sets are compared exactly (they are
+integer results, unique once sorted by (n, m, kind)); the survivor counts of
+the per-kind necessary conditions are compared exactly with the oracle's.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_pins import theorem1_pairs
+
+pytestmark = pytest.mark.gpu
+
+MAX_HI = (1 << 41) + (1 << 31)
+
+
+@pytest.fixture(scope="module")
+def B():
+    from paper_2506_01099_gb300 import benelux
+
+    return benelux
+
+
+@pytest.fixture(scope="module")
+def ctx(B):
+    c = B.Context(0, max_hi=MAX_HI)
+    yield c
+    c.close()
+
+
+def gpu_rad(ctx, lo, length):
+    import torch
+
+    rad = torch.empty(length, dtype=torch.int64, device="cuda")
+    sq = torch.empty(length, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    ctx.rad_segment(lo, length, rad.data_ptr(), sq.data_ptr(), stream)
+    torch.cuda.synchronize()
+    return rad.cpu().numpy().view(np.uint64), sq.cpu().numpy().view(np.uint64)
+
+
+def test_prime_count(ctx, orc):
+    assert ctx.prime_count() == orc.nprimes_upto(math.isqrt(MAX_HI))
+
+
+RAD_CASES = [
+    (1, 70_000),                      # start at 1, several tiles, ragged tail
+    (2, 1),                           # a single value
+    (9, 100),                         # starts on a prime square
+    (2**32 - 40_000, 90_001),         # across 2^32, several queue segments
+    (1048573**2 - 5000, 10_001),      # around a large prime square
+    (3**25 - 3000, 6000),             # around a high prime power
+    (2**40 - 2**13, 2**14 + 3),       # across 2^40
+    (1_400_000_000_000 - 4096, 8193),
+]
+
+
+@pytest.mark.parametrize("lo,length", RAD_CASES)
+def test_rad_segment_bit_exact(ctx, orc, lo, length):
+    rad, sq = gpu_rad(ctx, lo, length)
+    want = orc.rad_td_array(lo, length)
+    assert np.array_equal(rad, want), int(np.nonzero(rad != want)[0][0])
+    xs = np.arange(lo, lo + length, dtype=np.uint64)
+    assert np.array_equal(sq * rad, xs)
+
+
+def test_rad_segment_large_sampled(ctx, orc):
+    """A 2^27-value segment at 2^40 (many queue segments): sampled windows vs trial division."""
+    lo, length = 2**40 + 12345, 1 << 27
+    rad, _ = gpu_rad(ctx, lo, length)
+    rng = np.random.default_rng(5)
+    for off in list(rng.integers(0, length - 512, 12)) + [0, length - 512]:
+        off = int(off)
+        assert np.array_equal(rad[off:off + 512], orc.rad_td_array(lo + off, 512)), off
+
+
+@pytest.mark.parametrize("tune", [dict(tile_log2=12, seg_tiles=1, small_q_log2=10),
+                                  dict(tile_log2=14, seg_tiles=4, threads=1024, small_q_log2=16),
+                                  dict(tile_log2=11, seg_tiles=16, threads=256, small_q_log2=8)])
+def test_tunings_agree(B, orc, tune):
+    with B.Context(0, max_hi=1 << 41) as c:
+        c.set_tune(**tune)
+        for lo, length in [(1, 50_000), (2**40 - 20_000, 40_001)]:
+            rad, _ = gpu_rad(c, lo, length)
+            assert np.array_equal(rad, orc.rad_td_array(lo, length))
+        assert c.search(1, 1 << 20) == theorem1_pairs(1, 1 << 20)
+        assert c.search(2**40 - 2**21 - 8, 2**40 + 2**21 + 8) == theorem1_pairs(2**40 - 2**21 - 8, 2**40 + 2**21 + 8)
+
+
+def test_search_c1_full(ctx, orc):
+    """All n < 2^24, both kinds: equals the oracle and Theorem 1 (25 pairs)."""
+    got = ctx.search(1, 1 << 24)
+    assert got == orc.pairs_crt(1, 1 << 24)
+    assert got == theorem1_pairs(1, 1 << 24)
+    assert len(got) == 25
+    st = ctx.stats()
+    assert (st["survivors1"], st["survivors2"]) == orc.filter_counts(1, 1 << 24)
+
+
+@pytest.mark.parametrize("kinds", [1, 2])
+def test_search_single_kind(ctx, orc, kinds):
+    got = ctx.search(1, 1 << 22, kinds)
+    assert got == orc.pairs_crt(1, 1 << 22, kinds)
+    st = ctx.stats()
+    c1, c2 = orc.filter_counts(1, 1 << 22, kinds)
+    assert (st["survivors1"], st["survivors2"]) == (c1, c2)
+
+
+def test_filter_counts_high_window(ctx, orc):
+    lo, hi = 2**40 - 2**23, 2**40 + 2**23
+    got = ctx.search(lo, hi)
+    assert got == orc.pairs_crt(lo, hi)
+    st = ctx.stats()
+    assert (st["survivors1"], st["survivors2"]) == orc.filter_counts(lo, hi)
+
+
+def test_search_edges(ctx, orc):
+    # intervals whose ends sit exactly on pair members
+    for m, n, kind in theorem1_pairs(1, 1 << 40):
+        for lo, hi in ((n, n + 1), (n - 1, n), (n + 1, n + 2), (max(1, n - 3), n + 3)):
+            assert ctx.search(lo, hi) == theorem1_pairs(lo, hi), (lo, hi)
+    assert ctx.search(1, 2) == []
+    assert ctx.search(2, 4) == [(2, 3, 2)]
+    assert ctx.search(MAX_HI - 1000, MAX_HI) == orc.pairs_crt(MAX_HI - 1000, MAX_HI)
+
+
+def test_search_c2_full_range(ctx):
+    """All n < 2^32 (configured with 2^16-integer segments): the 33 pairs of Theorem 1."""
+    ctx.set_tune(tile_log2=13, seg_tiles=8)
+    got = ctx.search(1, 1 << 32)
+    assert got == theorem1_pairs(1, 1 << 32)
+    assert len(got) == 33
+
+
+def test_hash_search(ctx, orc):
+    assert ctx.search_hash(1 << 20) == orc.pairs_sort(1 << 20)
+    assert ctx.stats()["hash_keys"] == orc.hash_keys(1 << 20)
+    assert ctx.search_hash(1 << 24) == theorem1_pairs(1, 1 << 24)
+    assert ctx.search_hash(1 << 24, 2) == theorem1_pairs(1, 1 << 24, 2)
+
+
+def test_hash_search_c2(ctx):
+    assert ctx.search_hash(1 << 32) == theorem1_pairs(1, 1 << 32)
+
+
+def test_large_window_sample(ctx):
+    """The first 2^30 integers of [2^40, 2^40 + 2^37): exactly one second-kind pair."""
+    lo = 1 << 40
+    assert ctx.search(lo, lo + (1 << 30)) == [(1048577, 1099513724928, 2)]
+    hi = 1_400_000_000_000
+    assert ctx.search(hi - (1 << 28), hi) == []
+
+
+def test_batch_ragged_vs_oracle(ctx, orc):
+    ivs = [(1, 2, 3), (2, 4, 3), (5, 1000, 1), (1000, 70_000, 2), (1, 1 << 16, 3), (2**33 + 1, 2**33 + 77_777, 3),
+           (17179607040 - 100, 17179607040 + 1, 1), (17180131328, 17180131329, 2), (2**40 - 2**21, 2**40 - 2**21 + 1, 3),
+           (2**40 + 2**21 - 5, 2**40 + 2**21 + 5, 3)]
+    pairs, offs = ctx.batch(ivs)
+    assert len(offs) == len(ivs) + 1
+    for i, (lo, hi, k) in enumerate(ivs):
+        mine = [(m, n, kd) for (v, m, n, kd) in pairs[offs[i]:offs[i + 1]]]
+        assert all(v == i for (v, _, _, _) in pairs[offs[i]:offs[i + 1]])
+        assert mine == orc.pairs_crt(lo, hi, k), (lo, hi, k)
+
+
+def test_batch_equals_plain(ctx):
+    from paper_2506_01099_gb300 import workloads as W
+
+    ivs = [iv for iv in W.batch_intervals(256) if iv.length <= (1 << 24)][:64]
+    pairs, offs = ctx.batch(ivs)
+    for i, iv in enumerate(ivs):
+        mine = [(m, n, kd) for (_, m, n, kd) in pairs[offs[i]:offs[i + 1]]]
+        assert mine == ctx.search(iv.lo, iv.hi, iv.kinds)
+        assert mine == theorem1_pairs(iv.lo, iv.hi, iv.kinds)
+
+
+def test_batch_family_members(ctx):
+    """Intervals of the batched workload's shape placed on every family member above 2^32."""
+    ivs = []
+    for m, n, kind in theorem1_pairs(1 << 32, 1 << 41):
+        ivs.append((n - (1 << 16), n + (1 << 16), kind))
+        ivs.append((n - (1 << 20) + 7, n + 1, 3 - kind))  # the other kind: nothing
+    pairs, offs = ctx.batch(ivs)
+    for i, (lo, hi, k) in enumerate(ivs):
+        mine = [(m, n, kd) for (_, m, n, kd) in pairs[offs[i]:offs[i + 1]]]
+        assert mine == theorem1_pairs(lo, hi, k)
+
+
+def test_bad_arguments(B, ctx):
+    for args in ((0, 10, 3), (10, 10, 3), (5, 4, 3), (1, MAX_HI + 1, 3), (1, 10, 0), (1, 10, 4)):
+        with pytest.raises(B.BnxError) as e:
+            ctx.search(*args)
+        assert e.value.code == B.BNX_E_ARG
+
+
+def test_server_alone_vs_mix(B, ctx):
+    """Requests served concurrently return what each returns alone."""
+    reqs = [(2**40 - 2**23, 2**40 + 2**23, 3), (1, 1 << 22, 3), (2**36 - 5, 2**36 + 2**25, 2),
+            (17179607040 - 2**24, 17179607040 + 2**20, 1), (1_300_000_000_000, 1_300_000_000_000 + 2**26, 3)]
+    alone = [ctx.search(*r) for r in reqs]
+    B.bnx_server_start(ctx.h, max_active=3, slice_len=1 << 22)
+    try:
+        tickets = [B.bnx_server_submit(ctx.h, *r) for r in reqs]
+        got = {}
+        import time
+
+        t0 = time.time()
+        while len(got) < len(tickets) and time.time() - t0 < 120:
+            for t in tickets:
+                if t not in got:
+                    r = B.bnx_server_poll(ctx.h, t)
+                    if r is not None:
+                        got[t] = r
+            time.sleep(0.005)
+    finally:
+        B.bnx_server_stop(ctx.h)
+    assert len(got) == len(tickets)
+    for t, want in zip(tickets, alone):
+        pairs, lat = got[t]
+        assert pairs == want
+        assert lat > 0
