@@ -1,0 +1,438 @@
+"""Benchmark: integers searched per second for Benelux pairs near n = 2^40.
+
+Workload (one step): the batched configuration -- 4096 seeded intervals,
+lengths log-uniform in [2^16, 2^30], starts uniform in [2^32, 2^40), kind 1 or
+2 -- searched by one batched pipeline (bucket fill, one persistent sieve launch
+over the device segment queue, verification, device sort), replayed from a
+CUDA graph.  The same intervals are also searched by the plain path (one
+bnx_search per interval), the large window [2^40, 2^40 + 2^37) is run plain
+(one call) and batched (128 x 2^30), and a seeded Poisson request stream is
+served with continuous batching for p50/p99 latency.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU (torchrun): every rank searches its own 4096 intervals (seed + rank),
+no collective on the data path (weak scaling); value = all ranks' integers / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2506_01099_gb300 import workloads as W  # noqa: E402
+
+METRIC = "integers searched/s at n~2^40, batched (4096 seeded intervals in [2^32, 2^40))"
+UNIT = "integers/s"
+MAX_HI = (1 << 41) + (1 << 31)
+TUNE_CACHE = os.path.join(ROOT, "paper_2506_01099_gb300", "tune_cache.json")
+KERNELS_PER_STEP = 10  # plan, bucket count, 3 scan kernels, bucket fill, sieve, verify, sort, offsets
+# algorithmic integer lane-operations per searched integer ("Roofline"):
+#   init 1 + strikes 0.2732 * 5 + ctz 2 + key/filter 10  (odd prime powers: sum 1/(p(p-1)) = 0.2732)
+ALG_OPS_PER_INT = 1 + 0.2732 * 5 + 2 + 10
+SMS, LANES_PER_CLK, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            d = json.load(fh)
+        return d, "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": SM_MAX_MHZ}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi sampled every 200 ms during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.idx = gpu_index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                                          "-lms", "200", "-i", str(self.idx)], stdout=subprocess.PIPE,
+                                         stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        if self.t:
+            self.t.join(timeout=2)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            p = [x.strip() for x in ln.split(",")]
+            if len(p) < 9:
+                continue
+            try:
+                sm.append(float(p[1]))
+                smax = float(p[2])
+            except ValueError:
+                continue
+            for name, v in zip(names, p[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def load_tune(gpu_name: str) -> str | None:
+    try:
+        with open(TUNE_CACHE) as fh:
+            cache = json.load(fh)
+    except Exception:
+        return None
+    key = f"{gpu_name}|{MAX_HI.bit_length() - 1}"
+    t = cache.get(key)
+    return json.dumps(t) if t else None
+
+
+def dist_init():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl" if os.environ.get("BNX_BENCH_BACKEND") != "gloo" else "gloo")
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.barrier()
+
+
+def max_over_ranks(ws, x: float) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def sum_over_ranks(ws, x: float) -> float:
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+# ---------------------------------------------------------------------------
+# CPU baseline: the oracle as it stands, on a bounded sample of the workload
+# ---------------------------------------------------------------------------
+
+def oracle_sample(intervals, budget_integers: int):
+    """Leading pieces of the workload's intervals, clipped to budget_integers in total."""
+    out, tot = [], 0
+    for iv in intervals:
+        take = min(iv.hi - iv.lo, budget_integers - tot)
+        if take <= 0:
+            break
+        out.append(W.Interval(iv.lo, iv.lo + take, iv.kinds, iv.id))
+        tot += take
+    return out, tot
+
+
+def cpu_baseline(intervals, budget_integers: int):
+    import oracle
+
+    orc = oracle.load()
+    sample, tot = oracle_sample(intervals, budget_integers)
+    orc.lib.orc_init(2 * max(iv.hi for iv in sample) + 2)
+    t0 = time.perf_counter()
+    npairs = 0
+    for iv in sample:
+        npairs += len(orc.pairs_crt(iv.lo, iv.hi, iv.kinds))
+    dt = time.perf_counter() - t0
+    cores = os.cpu_count() or 1
+    return {"value": tot / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"first {tot} integers of the batched workload ({len(sample)} leading interval pieces), "
+                      f"{dt:.1f} s, CRT enumeration over Algorithm 1 radicals, OpenMP over 2^20-integer chunks",
+            "seconds": dt, "pairs": npairs}
+
+
+# ---------------------------------------------------------------------------
+
+def run_reference(args):
+    ws, rank, _ = dist_init()
+    if rank != 0:
+        return 0
+    ivs = W.batch_intervals(4096)
+    budget = int(args.ref_budget)
+    for _ in range(args.warmup):
+        cpu_baseline(ivs, budget // 8)
+    vals, secs = [], []
+    for _ in range(args.steps):
+        r = cpu_baseline(ivs, budget)
+        vals.append(r["value"])
+        secs.append(r["seconds"])
+    v = statistics.median(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "batched: 4096 intervals, len log-uniform [2^16, 2^30], lo uniform [2^32, 2^40), "
+                                   "kind 1|2 (seeded splitmix64); each step a bounded leading sample",
+                       "sample_integers": budget},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                             "sample": f"first {budget} integers of the batched workload per step"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    ws, rank, local = dist_init()
+    torch.cuda.set_device(local)
+    from paper_2506_01099_gb300 import benelux as B
+
+    gpu_name = torch.cuda.get_device_name(local)
+    tune_json = load_tune(gpu_name)
+    stream = torch.cuda.current_stream()
+    ctx = B.Context(local, max_hi=MAX_HI, tune_json=tune_json, stream=stream.cuda_stream)
+    if args.autotune:
+        sample = [iv for iv in W.batch_intervals(4096)][:512]
+        tj = ctx.autotune(sample, rounds=2)
+        if rank == 0:
+            print("autotuned:", tj, file=sys.stderr, flush=True)
+            try:
+                cache = json.load(open(TUNE_CACHE))
+            except Exception:
+                cache = {}
+            d = json.loads(tj)
+            d.pop("ms", None)
+            cache[f"{gpu_name}|{MAX_HI.bit_length() - 1}"] = d
+            json.dump(cache, open(TUNE_CACHE, "w"), indent=1, sort_keys=True)
+
+    seed = 3 ^ W.SEED_SALT
+    ivs = W.batch_intervals(4096, seed=seed + rank)
+    arr = B.make_intervals(ivs)
+    integers = W.total_integers(ivs)
+
+    for _ in range(args.warmup):
+        B.bnx_batch(ctx.h, ivs, arr)
+
+    sampler = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    barrier(ws)
+    torch.cuda.synchronize()
+    if sampler:
+        sampler.start()
+        time.sleep(0.3)
+    dev_ms, sieve_ms, wall = [], [], []
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    npairs = 0
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        pairs, offs = B.bnx_batch(ctx.h, ivs, arr)
+        wall.append(time.perf_counter() - t0)
+        st = ctx.stats()
+        dev_ms.append(st["ms_total"])
+        sieve_ms.append(st["ms_sieve"])
+        npairs = len(pairs)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier(ws)
+    clocks = sampler.stop() if sampler else None
+    loop_ms = e0.elapsed_time(e1)
+    st = ctx.stats()
+
+    # device-timed pipeline (inputs resident) and end-to-end through the public API
+    t_dev = max_over_ranks(ws, sum(dev_ms) / 1e3)
+    t_e2e = max_over_ranks(ws, sum(wall))
+    total_int = sum_over_ranks(ws, float(integers)) * args.steps
+    value = total_int / t_dev
+    e2e = total_int / t_e2e
+
+    extras = {}
+    if rank == 0 and not args.quick:
+        # plain path on the same intervals: one bnx_search per interval
+        for iv in ivs[:16]:
+            ctx.search(iv.lo, iv.hi, iv.kinds)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for iv in ivs:
+            ctx.search(iv.lo, iv.hi, iv.kinds)
+        tp = time.perf_counter() - t0
+        extras["plain_same_intervals"] = {"value": integers / tp, "unit": UNIT, "seconds": tp,
+                                          "note": "one blocking bnx_search per interval, same 4096 intervals"}
+        # the large window at 2^40, plain (one call) vs batched (128 x 2^30)
+        lo, hi = W.LARGE_WINDOWS[0]
+        ctx.search(lo, lo + (1 << 30))
+        t0 = time.perf_counter()
+        p_plain = ctx.search(lo, hi)
+        tpw = time.perf_counter() - t0
+        wivs = W.large_window_intervals(0)
+        warr = B.make_intervals(wivs)
+        B.bnx_batch(ctx.h, wivs, warr)
+        t0 = time.perf_counter()
+        p_b, _ = B.bnx_batch(ctx.h, wivs, warr)
+        tbw = time.perf_counter() - t0
+        extras["window_2p40"] = {"range": [lo, hi], "plain": (hi - lo) / tpw, "batched": (hi - lo) / tbw,
+                                 "unit": UNIT, "pairs_plain": len(p_plain), "pairs_batched": len(p_b)}
+        extras["serving"] = serve_stream(B, ctx, args, throughput=value / ws)
+
+    if rank == 0:
+        pk, pk_src = peaks()
+        ms_sieve = statistics.mean(sieve_ms)
+        sieve_rate = integers / (ms_sieve / 1e3)
+        alu_peak = SMS * LANES_PER_CLK * float(pk.get("sm_max_mhz", SM_MAX_MHZ)) * 1e6 / 1e12
+        achieved = sieve_rate * ALG_OPS_PER_INT / 1e12
+        cpu = None
+        if not args.no_cpu and ws == 1:
+            cpu = cpu_baseline(W.batch_intervals(4096), int(args.cpu_budget))
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+            "config": {"workload": "batched: 4096 intervals from seed, len log-uniform [2^16, 2^30], "
+                                   "lo uniform [2^32, 2^40), kind 1|2 50/50; one persistent launch, CUDA graph",
+                       "integers_per_step_per_gpu": integers, "tune": ctx.tune(),
+                       "l2": "no flush needed: each step rewrites GB-scale bucket arrays (>> 129 MB L2)",
+                       "parallelism": f"replicas x{ws} (independent intervals per GPU)"},
+            "e2e": {"value": e2e, "unit": UNIT, "h2d_bytes_per_step": 40 * len(ivs) + 4,
+                    "d2h_bytes_per_step": 128 + 24 * npairs + 8 * (len(ivs) + 1)},
+            "gpu_launches": KERNELS_PER_STEP * args.steps,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
+                         "frac": achieved / alu_peak, "traffic": None,
+                         "kernel": "k_sieve<search> (persistent tile sieve, fused filter + compaction)",
+                         "peak_source": "152 SMs x 128 lanes/clk x max SM clock (issue roofline)",
+                         "alg_ops_per_integer": ALG_OPS_PER_INT, "sieve_ms_per_launch": ms_sieve,
+                         "hbm_equivalent": {"achieved_gbs": sieve_rate * 8 / 1e9, "peak_gbs": pk["hbm_gbs"],
+                                            "frac": sieve_rate * 8 / 1e9 / pk["hbm_gbs"],
+                                            "note": f"8 B per integer vs {pk_src} copy bandwidth"}},
+            "clocks": clocks,
+            "device_loop_ms": loop_ms,
+            "stats": st,
+            "pairs_found": npairs,
+        }
+        if cpu:
+            line["cpu_baseline"] = cpu
+        line.update(extras)
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if ws > 1:
+        import torch.distributed as dist
+
+        dist.destroy_process_group()
+    return 0
+
+
+def serve_stream(B, ctx, args, throughput: float):
+    """Seeded Poisson stream at 0.7x the batched throughput; p50/p99 latency."""
+    n = args.serve_requests
+    mean_len = W.mean_serving_length()
+    rate = 0.7 * throughput / mean_len
+    reqs = W.serving_requests(n, rate_per_s=rate)
+    B.bnx_server_start(ctx.h, max_active=args.serve_slots, slice_len=args.serve_slice)
+    lat = {}
+    tickets = {}
+    t0 = time.perf_counter()
+    i = 0
+    integers = sum(r.interval.length for r in reqs)
+    try:
+        while len(lat) < n:
+            now = time.perf_counter() - t0
+            while i < n and reqs[i].arrival_s <= now:
+                iv = reqs[i].interval
+                tickets[B.bnx_server_submit(ctx.h, iv.lo, iv.hi, iv.kinds, iv.id)] = i
+                i += 1
+            for t in list(tickets):
+                r = B.bnx_server_poll(ctx.h, t)
+                if r is not None:
+                    lat[tickets.pop(t)] = r[1]
+            if time.perf_counter() - t0 > args.serve_timeout:
+                break
+            time.sleep(0.001)
+    finally:
+        B.bnx_server_stop(ctx.h)
+    span = time.perf_counter() - t0
+    ls = sorted(lat.values())
+    q = lambda p: ls[min(len(ls) - 1, int(math.ceil(p * len(ls))) - 1)] if ls else None
+    return {"requests": n, "completed": len(ls), "rate_per_s": rate, "p50_s": q(0.50), "p99_s": q(0.99),
+            "integers_per_s": integers / span, "span_s": span, "slots": args.serve_slots, "slice": args.serve_slice,
+            "note": "seeded Poisson arrivals at 0.7x batched throughput / E[len]; len log-uniform [2^20, 2^34], "
+                    "lo uniform [1, 1.4e12], kinds 1|2|3"}
+
+
+def profile_case():
+    import torch
+
+    from paper_2506_01099_gb300 import benelux as B
+
+    ctx = B.Context(0, max_hi=MAX_HI, tune_json=load_tune(torch.cuda.get_device_name(0)))
+    lo = 1 << 40
+    ctx.search(lo, lo + (1 << 20))
+    pairs = ctx.search(lo, lo + (1 << 28))
+    print(json.dumps({"profile_case": [lo, lo + (1 << 28)], "pairs": pairs, "stats": ctx.stats()}))
+    ctx.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--quick", action="store_true", help="timed batched steps only")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--autotune", action="store_true")
+    ap.add_argument("--cpu-budget", type=float, default=2 ** 34)
+    ap.add_argument("--ref-budget", type=float, default=2 ** 33)
+    ap.add_argument("--serve-requests", type=int, default=256)
+    ap.add_argument("--serve-slots", type=int, default=64)
+    ap.add_argument("--serve-slice", type=int, default=1 << 28)
+    ap.add_argument("--serve-timeout", type=float, default=120.0)
+    ap.add_argument("--profile-case", action="store_true",
+                    help="one warm-up and one search of [2^40, 2^40 + 2^28) (small case for ncu), then exit")
+    args = ap.parse_args()
+    if args.profile_case:
+        return profile_case()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())
