@@ -56,6 +56,7 @@ struct bnx_ctx {
     // device tables
     bnx::DevBuf primes, spp, lpp, tmp_counts;
     uint32_t np = 0, n_spp = 0, n_lpp = 0;
+    std::vector<uint32_t> h_spp_q; // in-tile q values (host copy)
     std::vector<uint64_t> lq;     // sorted large q (host copy)
     std::vector<double> lq_inv;   // prefix sums of 1/q over lq
 
@@ -86,6 +87,7 @@ struct bnx_ctx {
     bnx::Server *server = nullptr;
     std::atomic<bool> serving{false};
 
+    uint32_t n_sched() const { return bnx::sched_length(tune.tile_log2, h_spp_q.data(), n_spp); }
     uint32_t seg_log2() const {
         uint32_t l = 0;
         while ((1u << l) < tune.seg_tiles) l++;

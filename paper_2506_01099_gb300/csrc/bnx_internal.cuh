@@ -78,6 +78,7 @@ struct Plan {
     const uint32_t *n_iv;  // device: number of intervals in this run
     const SmallPP *spp;
     uint32_t n_spp;
+    uint32_t n_sched;  // length of the static strike schedule
     const LargePP *lpp;
     uint32_t n_lpp;
     uint32_t tile_log2, seg_log2;  // tile 2^tile_log2 integers, queue segment 2^seg_log2
@@ -124,7 +125,8 @@ void launch_plan(const Plan &P, uint32_t *n_iv_dev, IvDev *ivs, uint64_t max_iv,
 void launch_bucket(const Plan &P, bool fill, int grid, cudaStream_t s);
 void launch_sieve(const Plan &P, int mode, int grid, int threads, size_t smem, cudaStream_t s);
 int sieve_occupancy(int mode, int threads, size_t smem, int *ctas_per_sm);
-size_t sieve_smem_bytes(uint32_t tile_log2);
+size_t sieve_smem_bytes(uint32_t tile_log2, uint32_t nspp, uint32_t nsched);
+uint32_t sched_length(uint32_t tile_log2, const uint32_t *q, uint32_t nspp);
 
 // verify.cu
 void launch_verify(const Plan &P, int grid, cudaStream_t s);

@@ -118,6 +118,10 @@ int build_pp_tables(bnx_ctx *c) {
     if (h[1] > lpp_cap) return fail(BNX_E_NOMEM, "large prime-power table overflow");
     c->n_spp = h[0];
     c->n_lpp = h[1];
+    std::vector<SmallPP> hs(c->n_spp);
+    if (c->n_spp) CUDA_TRY(cudaMemcpy(hs.data(), c->spp.p, sizeof(SmallPP) * c->n_spp, cudaMemcpyDeviceToHost));
+    c->h_spp_q.resize(c->n_spp);
+    for (uint32_t i = 0; i < c->n_spp; i++) c->h_spp_q[i] = hs[i].q;
     // host copy of the large q values, sorted, for the bucket capacity bound
     std::vector<LargePP> tmp(c->n_lpp);
     if (c->n_lpp)
@@ -225,6 +229,7 @@ Plan make_plan(const bnx_ctx *c) {
     P.n_iv = (const uint32_t *)c->n_iv.p;
     P.spp = (const SmallPP *)c->spp.p;
     P.n_spp = c->n_spp;
+    P.n_sched = c->n_sched();
     P.lpp = (const LargePP *)c->lpp.p;
     P.n_lpp = c->n_lpp;
     P.tile_log2 = c->tune.tile_log2;
@@ -262,11 +267,12 @@ Plan make_plan(const bnx_ctx *c) {
 // any stream capture and cached until the tuning changes).
 int sieve_config(bnx_ctx *c, int mode, int *grid, int *threads, size_t *smem) {
     SieveCfg &sc = c->sieve_cfg[mode];
+    const size_t want_smem = sieve_smem_bytes(c->tune.tile_log2, c->n_spp, c->n_sched());
     if (!sc.valid || sc.tile_log2 != c->tune.tile_log2 || sc.threads != c->tune.threads ||
-        sc.ctas != c->tune.ctas_per_sm) {
+        sc.ctas != c->tune.ctas_per_sm || sc.smem != want_smem) {
         if (c->capturing) return fail(BNX_E_STATE, "sieve launch shape unknown during capture");
         const int thr = (int)c->tune.threads;
-        const size_t smem_b = sieve_smem_bytes(c->tune.tile_log2);
+        const size_t smem_b = want_smem;
         int occ = 0;
         int e = sieve_occupancy(mode, thr, smem_b, &occ);
         if (e != 0) return fail(BNX_E_CUDA, "sieve occupancy query failed: %s", cudaGetErrorString((cudaError_t)e));

@@ -36,15 +36,6 @@ __device__ __forceinline__ uint32_t ctz64(uint64_t x) { return (uint32_t)(__ffsl
 __device__ __forceinline__ uint32_t bitlen64(uint64_t x) { return 64u - (uint32_t)__clzll((long long)x); }
 __device__ __forceinline__ uint32_t flog2_64(uint64_t x) { return 63u - (uint32_t)__clzll((long long)x); }
 
-// s[x] *= p, atomically (strikes of different prime powers may meet at x)
-__device__ __forceinline__ void smul(unsigned long long *a, unsigned long long p) {
-    unsigned long long old = *a, assumed;
-    do {
-        assumed = old;
-        old = atomicCAS(a, assumed, assumed * p);
-    } while (old != assumed);
-}
-
 // index of the interval owning item `x`: the last v with base(v) <= x
 template <bool SEG>
 __device__ __forceinline__ uint32_t find_iv(const IvDev *ivs, uint32_t k, uint64_t x) {
@@ -168,27 +159,36 @@ __global__ void __launch_bounds__(256) k_bucket(Plan P) {
 }
 
 // --------------------------------------------------------------- sieve ----
-// Shared memory: the tile, then per in-tile prime power q, p, the offset of its
-// first multiple in the current tile, L_tile mod q, its hit count and
-// warp-chunk prefix, and the list of warp-chunks of the current tile.
-constexpr int kMaxChunks = 1024;
+// Shared memory of one CTA (sizes from the tile length, the number of in-tile
+// prime powers and the length of the static strike schedule):
+//   tile    u64[L_tile + 2]   s[x] for the values t_lo .. t_lo + tl
+//   bitmap  u32[L_tile/32+2]  candidate n of the tile (search and hash modes)
+//   sq, sp, soff, slmod       per in-tile prime power: q, p, first multiple in
+//                             the current tile, L_tile mod q
+//   sched   u16[n_chunks]     static strike schedule: (prime power j, chunk c);
+//                             chunk c of q covers its multiples 32c .. 32c+31
+//   bcache  uint2[256]        the segment's bucket entries
+constexpr int kBucketCache = 256;
+constexpr uint32_t kHighTwoLog2 = 9;  // n with 2^9 | n or 2^9 | n+1 are always checked
 
 struct SmemLayout {
-    size_t tile_bytes;
-    size_t total;
+    size_t tile, bitmap, spp, sched, bcache, total;
 };
 
-__host__ __device__ inline SmemLayout smem_layout(uint32_t tile_log2) {
+__host__ __device__ inline size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+__host__ __device__ inline SmemLayout smem_layout(uint32_t tile_log2, uint32_t nspp, uint32_t nsched) {
     SmemLayout L;
-    L.tile_bytes = (((size_t)1 << tile_log2) + 2) * sizeof(unsigned long long);
-    L.tile_bytes = (L.tile_bytes + 15) & ~(size_t)15;
-    L.total = L.tile_bytes + (size_t)6 * kMaxSpp * sizeof(uint32_t) + sizeof(uint32_t) * (kMaxSpp + 1) +
-              sizeof(uint32_t) * kMaxChunks;
+    L.tile = 0;
+    L.bitmap = L.tile + align16((((size_t)1 << tile_log2) + 2) * sizeof(unsigned long long));
+    L.spp = L.bitmap + align16((((size_t)1 << tile_log2) / 32 + 2) * sizeof(uint32_t));
+    L.sched = L.spp + align16((size_t)4 * (nspp ? nspp : 1) * sizeof(uint32_t));
+    L.bcache = L.sched + align16((size_t)(nsched ? nsched : 1) * sizeof(uint16_t));
+    L.total = L.bcache + (size_t)kBucketCache * sizeof(uint2);
     return L;
 }
 
-// exact decision for one n whose bit-length bound did not reject it
-// s0, s1: odd square parts of n and n+1 (from the tile)
+// exact decision for one candidate n (s0, s1: odd square parts of n and n+1)
 __device__ __noinline__ uint32_t exact_kinds(uint64_t n, uint64_t s0, uint64_t s1, uint32_t kinds, int mode,
                                              uint64_t hash_S, uint64_t *pa, uint64_t *pb) {
     const uint32_t t0 = ctz64(n), t1 = ctz64(n + 1);
@@ -209,27 +209,49 @@ __device__ __noinline__ uint32_t exact_kinds(uint64_t n, uint64_t s0, uint64_t s
     return r;
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(1024) k_sieve(Plan P) {
+// s[x] *= p.  With MARK, the strike that lifts s[x] across tau marks n = x and
+// n = x - 1 as candidates (s only grows, so exactly one strike crosses).
+template <bool MARK>
+__device__ __forceinline__ void strike(unsigned long long *tile, uint32_t *bitmap, uint32_t x, uint32_t p,
+                                       unsigned long long tau, uint32_t tl) {
+    unsigned long long old = tile[x], assumed;
+    do {
+        assumed = old;
+        old = atomicCAS(&tile[x], assumed, assumed * p);
+    } while (old != assumed);
+    if (MARK && assumed < tau && assumed * p >= tau) {
+        if (x < tl) atomicOr(&bitmap[x >> 5], 1u << (x & 31));
+        if (x > 0) atomicOr(&bitmap[(x - 1) >> 5], 1u << ((x - 1) & 31));
+    }
+}
+
+template <int NT>
+struct MinBlocks {
+    static constexpr int value = NT <= 128 ? 8 : NT <= 256 ? 6 : NT <= 512 ? 3 : 1;
+};
+
+template <int MODE, int NT>
+__global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_sieve(Plan P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr bool MARK = MODE != kModeRad;
     const uint32_t tile_log2 = P.tile_log2;
     const uint32_t LT = 1u << tile_log2;
-    const SmemLayout lay = smem_layout(tile_log2);
-    unsigned long long *tile = reinterpret_cast<unsigned long long *>(smem_raw);
-    uint32_t *sq = reinterpret_cast<uint32_t *>(smem_raw + lay.tile_bytes);
-    uint32_t *sp = sq + kMaxSpp;
-    uint32_t *soff = sp + kMaxSpp;
-    uint32_t *slmod = soff + kMaxSpp;
-    uint32_t *scnt = slmod + kMaxSpp;
-    uint32_t *sc = scnt + kMaxSpp;      // warp-chunks per prime power (scratch)
-    uint32_t *spre = sc + kMaxSpp;      // kMaxSpp + 1
-    uint32_t *schunks = spre + kMaxSpp + 1;
-    __shared__ unsigned long long s_seg;
-    __shared__ uint32_t s_iv, s_nchunks;
-
-    const uint32_t tid = threadIdx.x, NT = blockDim.x;
-    const uint32_t lane = tid & 31, warp = tid >> 5, nwarps = NT >> 5;
     const uint32_t nspp = P.n_spp;
+    const SmemLayout lay = smem_layout(tile_log2, nspp, P.n_sched);
+    unsigned long long *tile = reinterpret_cast<unsigned long long *>(smem_raw + lay.tile);
+    uint32_t *bitmap = reinterpret_cast<uint32_t *>(smem_raw + lay.bitmap);
+    uint32_t *sq = reinterpret_cast<uint32_t *>(smem_raw + lay.spp);
+    uint32_t *sp = sq + nspp;
+    uint32_t *soff = sp + nspp;
+    uint32_t *slmod = soff + nspp;
+    uint16_t *sched = reinterpret_cast<uint16_t *>(smem_raw + lay.sched);
+    uint2 *bcache = reinterpret_cast<uint2 *>(smem_raw + lay.bcache);
+    __shared__ unsigned long long s_seg;
+    __shared__ uint32_t s_iv, s_nsched;
+
+    const uint32_t tid = threadIdx.x;
+    const uint32_t lane = tid & 31, warp = tid >> 5;
+    constexpr uint32_t nwarps = NT / 32;
     const uint32_t k = *P.n_iv;
     const unsigned long long total_segs = P.ctr->total_segs;
 
@@ -239,9 +261,37 @@ __global__ void __launch_bounds__(1024) k_sieve(Plan P) {
         sp[j] = e.p;
         slmod[j] = LT % e.q;
     }
+    __syncthreads();
+    if (warp == 0) {
+        // static schedule: prime power j has at most floor(L_tile/q)+1 multiples
+        // in a tile, i.e. ceil((floor(L_tile/q)+1)/32) warp-chunks
+        constexpr int kPer = kMaxSpp / 32;
+        uint32_t v[kPer];
+        uint32_t sum = 0;
+#pragma unroll
+        for (int u = 0; u < kPer; u++) {
+            const uint32_t j = lane * kPer + u;
+            v[u] = j < nspp ? (LT / sq[j] + 1 + 31) / 32 : 0;
+            sum += v[u];
+        }
+        uint32_t inc = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t x = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= (uint32_t)o) inc += x;
+        }
+        uint32_t run = inc - sum;
+#pragma unroll
+        for (int u = 0; u < kPer; u++) {
+            const uint32_t j = lane * kPer + u;
+            for (uint32_t c = 0; c < v[u]; c++)
+                if (run + c < P.n_sched) sched[run + c] = (uint16_t)(j | (c << 8));
+            run += v[u];
+        }
+        if (lane == 31) s_nsched = inc < P.n_sched ? inc : P.n_sched;
+    }
 
     for (;;) {
-        __syncthreads();  // previous segment fully done (tile, tables)
+        __syncthreads();  // previous segment done
         if (tid == 0) {
             s_seg = atomicAdd(&P.ctr->queue_head, 1ull);
             s_iv = s_seg < total_segs ? find_iv<true>(P.ivs, k, s_seg) : 0;
@@ -254,68 +304,77 @@ __global__ void __launch_bounds__(1024) k_sieve(Plan P) {
         const uint64_t rem = iv.hi - seg_lo;
         const uint32_t seg_len = rem < (1ull << P.seg_log2) ? (uint32_t)rem : (1u << P.seg_log2);
         const unsigned long long b0 = P.boff[seg], b1 = P.boff[seg + 1];
-
+        const uint32_t nb_cached = (uint32_t)((b1 - b0) < (unsigned long long)kBucketCache ? (b1 - b0) : kBucketCache);
         for (uint32_t j = tid; j < nspp; j += NT) {
             const uint32_t q = sq[j];
             const uint32_t r = (uint32_t)(seg_lo % q);
             soff[j] = r ? q - r : 0;
         }
+        for (uint32_t e = tid; e < nb_cached; e += NT) bcache[e] = P.bent[b0 + e];
+        const uint32_t nsched = s_nsched;
+        const uint32_t kinds = iv.kinds;
 
         for (uint32_t t0 = 0; t0 < seg_len; t0 += LT) {
-            // tile: n in [t_lo, t_lo + tl), values t_lo .. t_lo + tl (halo)
+            // tile: n in [t_lo, t_lo + tl); values t_lo .. t_lo + tl (the last is the halo)
             const uint32_t tl = (seg_len - t0) < LT ? (seg_len - t0) : LT;
             const uint64_t t_lo = seg_lo + t0;
-            __syncthreads();  // offsets written, previous tile's epilogue done
-            for (uint32_t i = tid; i <= tl; i += NT) tile[i] = 1ull;
-            for (uint32_t j = tid; j < nspp; j += NT) {
-                const uint32_t off = soff[j];
-                const uint32_t cnt = off <= tl ? (tl - off) / sq[j] + 1 : 0;
-                scnt[j] = cnt;
-                sc[j] = (cnt + 31) >> 5;
+            const uint32_t nwords = (tl + 31) >> 5;
+            // Candidate threshold tau (uniform per tile).  An n with s(n), s(n+1)
+            // < tau and 2^9 dividing neither n nor n+1 has
+            // s(n)s(n+1) < tau^2 2^7 (the power of 2 included); tau is the largest
+            // power of two for which that bound already fails the filter at the
+            // tile's smallest n.  tau = 0: every n is a candidate.
+            unsigned long long tau = ~0ull;
+            if (MARK) {
+                int v;
+                if (MODE == kModeSearch) {
+                    // need 2 s(n)s(n+1) >= n+1:  tau^2 2^8 <= t_lo + 1
+                    v = (int)flog2_64(t_lo + 1) - (int)kHighTwoLog2 + 1;
+                } else {
+                    // need s(n)s(n+1) >= n(n+1)/(2S):  tau^2 2^7 <= t_lo(t_lo+1)/(2S)
+                    const uint64_t S2 = 2 * P.hash_S;
+                    const int clog = (int)flog2_64(S2) + ((S2 & (S2 - 1)) ? 1 : 0);
+                    v = (int)flog2_64(t_lo) + (int)flog2_64(t_lo + 1) - clog - (int)kHighTwoLog2 + 2;
+                }
+                tau = v >= 2 ? (1ull << (v / 2 < 62 ? v / 2 : 62)) : 0ull;
             }
-            __syncthreads();
-            if (warp == 0) {
-                // exclusive scan of the warp-chunk counts, then the chunk list
-                constexpr int kPer = kMaxSpp / 32;
-                uint32_t v[kPer];
-                uint32_t sum = 0;
-#pragma unroll
-                for (int u = 0; u < kPer; u++) {
-                    const uint32_t j = lane * kPer + u;
-                    v[u] = j < nspp ? sc[j] : 0;
-                    sum += v[u];
+            // bit-length reject for single candidates: s(n)s(n+1) < 2^lb fails the
+            // filter when lb <= thr_lb (search: 2^(lb+1) <= n+1; hash: 2^lb <= n(n+1)/(2S))
+            int thr_lb = 0;
+            if (MODE == kModeSearch) {
+                thr_lb = (int)flog2_64(t_lo + 1) - 1;
+            } else if (MODE == kModeHash) {
+                const uint64_t S2 = 2 * P.hash_S;
+                const int clog = (int)flog2_64(S2) + ((S2 & (S2 - 1)) ? 1 : 0);
+                thr_lb = (int)flog2_64(t_lo) + (int)flog2_64(t_lo + 1) - clog;
+            }
+            __syncthreads();  // offsets and bucket cache ready, previous tile's epilogue done
+            {
+                // vectorised init: s = 1 for values 0 .. tl
+                ulonglong2 *t2 = reinterpret_cast<ulonglong2 *>(tile);
+                const ulonglong2 one = make_ulonglong2(1ull, 1ull);
+                for (uint32_t i = tid; i <= (tl >> 1); i += NT) t2[i] = one;
+                if (MARK) {
+                    const uint32_t fill = tau == 0 ? ~0u : 0u;
+                    for (uint32_t w = tid; w < nwords; w += NT) bitmap[w] = fill;
                 }
-                uint32_t inc = sum;
-                for (int o = 1; o < 32; o <<= 1) {
-                    const uint32_t x = __shfl_up_sync(0xffffffffu, inc, o);
-                    if (lane >= (uint32_t)o) inc += x;
-                }
-                uint32_t run = inc - sum;
-#pragma unroll
-                for (int u = 0; u < kPer; u++) {
-                    const uint32_t j = lane * kPer + u;
-                    if (j < nspp) {
-                        spre[j] = run;
-                        for (uint32_t c = 0; c < v[u]; c++)
-                            if (run + c < kMaxChunks) schunks[run + c] = j | (c << 8);
-                    }
-                    run += v[u];
-                }
-                if (lane == 31) s_nchunks = inc < kMaxChunks ? inc : kMaxChunks;
             }
             __syncthreads();
             // small prime powers: one warp-chunk = 32 consecutive multiples of q
-            const uint32_t nch = s_nchunks;
-            for (uint32_t g = warp; g < nch; g += nwarps) {
-                const uint32_t e = schunks[g];
+            for (uint32_t g = warp; g < nsched; g += nwarps) {
+                const uint32_t e = sched[g];
                 const uint32_t j = e & 255u;
-                const uint32_t i = ((e >> 8) << 5) + lane;
-                if (i < scnt[j]) smul(&tile[soff[j] + i * sq[j]], sp[j]);
+                const uint32_t x = soff[j] + (((e >> 8) << 5) + lane) * sq[j];
+                if (x <= tl) strike<MARK>(tile, bitmap, x, sp[j], tau, tl);
             }
-            // large prime powers from this segment's bucket
-            for (unsigned long long e = b0 + tid; e < b1; e += NT) {
+            // large prime powers: this segment's bucket
+            for (uint32_t e = tid; e < nb_cached; e += NT) {
+                const uint2 h = bcache[e];
+                if (h.x >= t0 && h.x <= t0 + tl) strike<MARK>(tile, bitmap, h.x - t0, h.y, tau, tl);
+            }
+            for (unsigned long long e = b0 + kBucketCache + tid; e < b1; e += NT) {
                 const uint2 h = P.bent[e];
-                if (h.x >= t0 && h.x <= t0 + tl) smul(&tile[h.x - t0], h.y);
+                if (h.x >= t0 && h.x <= t0 + tl) strike<MARK>(tile, bitmap, h.x - t0, h.y, tau, tl);
             }
             __syncthreads();
             // offsets of the next tile: (off - L_tile) mod q
@@ -336,31 +395,36 @@ __global__ void __launch_bounds__(1024) k_sieve(Plan P) {
                     }
                 }
             } else {
-                // bit-length bound: s(n)s(n+1) < 2^bits with s including the 2-part
-                int thr;
-                if (MODE == kModeSearch) {
-                    thr = (int)flog2_64(t_lo + 1);  // reject when 2^(bits+1) <= n+1
-                } else {
-                    const uint64_t S2 = 2 * P.hash_S;
-                    const int clog = (int)flog2_64(S2) + ((S2 & (S2 - 1)) ? 1 : 0);
-                    thr = (int)flog2_64(t_lo) + (int)flog2_64(t_lo + 1) - clog;  // reject when bits <= thr
-                }
-                const uint32_t kinds = iv.kinds;
-                for (uint32_t base = 0; base < tl; base += NT) {
-                    const uint32_t i = base + tid;
-                    bool cand = false;
-                    uint64_t n = 0, s0 = 0, s1 = 0;
-                    if (i < tl) {
-                        s0 = tile[i];
-                        s1 = tile[i + 1];
-                        n = t_lo + i;
-                        const int bits = (int)(bitlen64(s0) + bitlen64(s1) + ctz64(n + (n & 1)) - 1);
-                        cand = MODE == kModeSearch ? (bits + 1 > thr) : (bits > thr);
+                // sparse epilogue: only the marked n and the n next to a multiple of 2^9
+                constexpr uint32_t M2 = 1u << kHighTwoLog2;
+                for (uint32_t w0 = warp * 32; w0 < nwords; w0 += nwarps * 32) {
+                    const uint32_t w = w0 + lane;
+                    uint32_t bits = 0;
+                    if (w < nwords) {
+                        bits = bitmap[w];
+                        if (tau != 0) {
+                            const uint32_t r = (uint32_t)((t_lo + 32ull * w) & (M2 - 1));
+                            const uint32_t d0 = (M2 - r) & (M2 - 1);  // bit of the n with 2^9 | n
+                            const uint32_t d1 = (d0 + M2 - 1) & (M2 - 1);  // bit of the n with 2^9 | n+1
+                            if (d0 < 32) bits |= 1u << d0;
+                            if (d1 < 32) bits |= 1u << d1;
+                        }
+                        const uint32_t lim = tl - 32 * w;  // >= 1
+                        if (lim < 32) bits &= (1u << lim) - 1;
                     }
-                    if (__any_sync(0xffffffffu, cand)) {
+                    while (__any_sync(0xffffffffu, bits != 0)) {
                         uint32_t kk = 0;
-                        uint64_t a = 0, b = 0;
-                        if (cand) kk = exact_kinds(n, s0, s1, kinds, MODE, P.hash_S, &a, &b);
+                        uint64_t n = 0, a = 0, b = 0;
+                        if (bits) {
+                            const uint32_t i = 32 * w + (uint32_t)(__ffs(bits) - 1);
+                            bits &= bits - 1;
+                            n = t_lo + i;
+                            const uint64_t s0 = tile[i], s1 = tile[i + 1];
+                            // bit-length bound first: s(n)s(n+1) < 2^lb, power of 2 included
+                            const int lb = (int)(bitlen64(s0) + bitlen64(s1) + ctz64(n + (n & 1))) - 1;
+                            if (lb > thr_lb) kk = exact_kinds(n, s0, s1, kinds, MODE, P.hash_S, &a, &b);
+                        }
+                        // warp-ballot compaction: one atomic per warp
                         const uint32_t m = __ballot_sync(0xffffffffu, kk != 0);
                         if (m) {
                             unsigned long long wbase = 0;
@@ -392,9 +456,33 @@ __global__ void __launch_bounds__(1024) k_sieve(Plan P) {
     }
 }
 
+template <int MODE>
+const void *sieve_fn_t(int threads) {
+    switch (threads) {
+        case 128: return (const void *)k_sieve<MODE, 128>;
+        case 256: return (const void *)k_sieve<MODE, 256>;
+        case 512: return (const void *)k_sieve<MODE, 512>;
+        default: return (const void *)k_sieve<MODE, 1024>;
+    }
+}
+
+const void *sieve_fn(int mode, int threads) {
+    if (mode == kModeRad) return sieve_fn_t<kModeRad>(threads);
+    if (mode == kModeHash) return sieve_fn_t<kModeHash>(threads);
+    return sieve_fn_t<kModeSearch>(threads);
+}
+
 }  // namespace
 
-size_t sieve_smem_bytes(uint32_t tile_log2) { return smem_layout(tile_log2).total; }
+uint32_t sched_length(uint32_t tile_log2, const uint32_t *q, uint32_t nspp) {
+    uint32_t n = 0;
+    for (uint32_t j = 0; j < nspp; j++) n += (((1u << tile_log2) / q[j]) + 1 + 31) / 32;
+    return n;
+}
+
+size_t sieve_smem_bytes(uint32_t tile_log2, uint32_t nspp, uint32_t nsched) {
+    return smem_layout(tile_log2, nspp, nsched).total;
+}
 
 void launch_plan(const Plan &P, uint32_t *n_iv_dev, IvDev *ivs, uint64_t max_iv, cudaStream_t s) {
     (void)max_iv;
@@ -406,23 +494,16 @@ void launch_bucket(const Plan &P, bool fill, int grid, cudaStream_t s) {
     else k_bucket<false><<<grid, 256, 0, s>>>(P);
 }
 
-static const void *sieve_fn(int mode) {
-    if (mode == kModeRad) return (const void *)k_sieve<kModeRad>;
-    if (mode == kModeHash) return (const void *)k_sieve<kModeHash>;
-    return (const void *)k_sieve<kModeSearch>;
-}
-
 int sieve_occupancy(int mode, int threads, size_t smem, int *ctas_per_sm) {
-    const void *fn = sieve_fn(mode);
+    const void *fn = sieve_fn(mode, threads);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, fn, threads, smem);
 }
 
 void launch_sieve(const Plan &P, int mode, int grid, int threads, size_t smem, cudaStream_t s) {
-    if (mode == kModeRad) k_sieve<kModeRad><<<grid, threads, smem, s>>>(P);
-    else if (mode == kModeHash) k_sieve<kModeHash><<<grid, threads, smem, s>>>(P);
-    else k_sieve<kModeSearch><<<grid, threads, smem, s>>>(P);
+    void *args[] = {(void *)&P};
+    cudaLaunchKernel(sieve_fn(mode, threads), dim3(grid), dim3(threads), args, smem, s);
 }
 
 }  // namespace bnx
