@@ -74,7 +74,9 @@ typedef struct {
     uint32_t threads;      /* threads per CTA (256, 512 or 1024) */
     uint32_t ctas_per_sm;  /* resident CTAs per SM for the persistent grid (0 = occupancy limit) */
     uint32_t small_q_log2; /* prime powers q <= 2^small_q_log2 are struck in shared
-                              memory, larger ones come from the HBM buckets (8..20) */
+                              memory, larger ones come from the HBM buckets (8..16) */
+    uint32_t exact_tile;   /* searches: 0 = log-domain u32 tile with exact re-check of
+                              candidates (default), 1 = exact u64 square-part tile */
 } bnx_tune;
 
 /* Per-call counters of the last search on a context. */

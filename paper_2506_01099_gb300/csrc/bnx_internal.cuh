@@ -21,9 +21,15 @@ namespace bnx {
 constexpr int kMaxSpp = 256;    // in-tile prime powers per context
 constexpr int kMaxThreads = 1024;
 
+// Fixed-point scale of the log-domain tile: lg(p) = floor(log2(p) * 2^16) + 1,
+// strictly above log2(p) * 2^16.
+constexpr uint32_t kLogFrac = 16;
+
 struct SmallPP {
-    uint32_t q;  // p^k
+    uint32_t q;   // p^k
     uint32_t p;
+    uint32_t lg;  // log2(p) rounded up in units of 2^-16
+    uint32_t k;   // exponent
 };
 
 struct LargePP {
@@ -79,6 +85,7 @@ struct Plan {
     const SmallPP *spp;
     uint32_t n_spp;
     uint32_t n_sched;  // length of the static strike schedule
+    uint32_t sqrt_q;   // floor(sqrt(Q)): primes above it reach the tile only through buckets
     const LargePP *lpp;
     uint32_t n_lpp;
     uint32_t tile_log2, seg_log2;  // tile 2^tile_log2 integers, queue segment 2^seg_log2
@@ -107,6 +114,8 @@ struct Plan {
 };
 
 enum SieveMode { kModeSearch = 0, kModeRad = 1, kModeHash = 2 };
+// which tile the search and hash modes use
+enum TileKind { kTileLog = 0, kTileExact = 1 };
 
 // ---------------------------------------------------------------- kernels --
 // tables.cu
@@ -125,6 +134,10 @@ void launch_plan(const Plan &P, uint32_t *n_iv_dev, IvDev *ivs, uint64_t max_iv,
 void launch_bucket(const Plan &P, bool fill, int grid, cudaStream_t s);
 void launch_sieve(const Plan &P, int mode, int grid, int threads, size_t smem, cudaStream_t s);
 int sieve_occupancy(int mode, int threads, size_t smem, int *ctas_per_sm);
+// sieve_log.cu: log-domain tile for the search and hash modes
+void launch_sieve_log(const Plan &P, int mode, int grid, int threads, size_t smem, cudaStream_t s);
+int sieve_log_occupancy(int mode, int threads, size_t smem, int *ctas_per_sm);
+size_t sieve_log_smem_bytes(uint32_t tile_log2, uint32_t nspp, uint32_t nsched);
 size_t sieve_smem_bytes(uint32_t tile_log2, uint32_t nspp, uint32_t nsched);
 uint32_t sched_length(uint32_t tile_log2, const uint32_t *q, uint32_t nspp);
 

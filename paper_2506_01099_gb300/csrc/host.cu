@@ -60,6 +60,7 @@ static void tune_defaults(bnx_tune *t) {
     t->threads = 512;
     t->ctas_per_sm = 0;
     t->small_q_log2 = 14;
+    t->exact_tile = 0;
 }
 
 static int tune_check(const bnx_tune *t) {
@@ -68,7 +69,8 @@ static int tune_check(const bnx_tune *t) {
         return fail(BNX_E_ARG, "seg_tiles must be a power of two in [1, 64]");
     if (t->threads != 128 && t->threads != 256 && t->threads != 512 && t->threads != 1024)
         return fail(BNX_E_ARG, "threads must be 128, 256, 512 or 1024");
-    if (t->small_q_log2 < 8 || t->small_q_log2 > 20) return fail(BNX_E_ARG, "small_q_log2 must be in [8, 20]");
+    if (t->small_q_log2 < 8 || t->small_q_log2 > 16) return fail(BNX_E_ARG, "small_q_log2 must be in [8, 16]");
+    if (t->exact_tile > 1) return fail(BNX_E_ARG, "exact_tile must be 0 or 1");
     if (t->ctas_per_sm > 32) return fail(BNX_E_ARG, "ctas_per_sm must be <= 32");
     return BNX_OK;
 }
@@ -82,7 +84,8 @@ static int parse_tune_json(const char *s, bnx_tune *t) {
                   {"seg_tiles", &t->seg_tiles},
                   {"threads", &t->threads},
                   {"ctas_per_sm", &t->ctas_per_sm},
-                  {"small_q_log2", &t->small_q_log2}};
+                  {"small_q_log2", &t->small_q_log2},
+                  {"exact_tile", &t->exact_tile}};
     for (const F &f : fields) {
         std::string key = std::string("\"") + f.name + "\"";
         const char *p = strstr(s, key.c_str());
@@ -230,6 +233,11 @@ Plan make_plan(const bnx_ctx *c) {
     P.spp = (const SmallPP *)c->spp.p;
     P.n_spp = c->n_spp;
     P.n_sched = c->n_sched();
+    {
+        uint32_t r = 1u << (c->tune.small_q_log2 / 2);
+        while ((uint64_t)(r + 1) * (r + 1) <= (1ull << c->tune.small_q_log2)) r++;
+        P.sqrt_q = r;
+    }
     P.lpp = (const LargePP *)c->lpp.p;
     P.n_lpp = c->n_lpp;
     P.tile_log2 = c->tune.tile_log2;
@@ -265,16 +273,20 @@ Plan make_plan(const bnx_ctx *c) {
 
 // Launch shape of the persistent sieve for the current tuning (queried outside
 // any stream capture and cached until the tuning changes).
+static bool use_log_tile(const bnx_ctx *c, int mode) { return mode != kModeRad && c->tune.exact_tile == 0; }
+
 int sieve_config(bnx_ctx *c, int mode, int *grid, int *threads, size_t *smem) {
-    SieveCfg &sc = c->sieve_cfg[mode];
-    const size_t want_smem = sieve_smem_bytes(c->tune.tile_log2, c->n_spp, c->n_sched());
+    const bool lg = use_log_tile(c, mode);
+    SieveCfg &sc = c->sieve_cfg[mode * 2 + (lg ? 1 : 0)];
+    const size_t want_smem = lg ? sieve_log_smem_bytes(c->tune.tile_log2, c->n_spp, c->n_sched())
+                                : sieve_smem_bytes(c->tune.tile_log2, c->n_spp, c->n_sched());
     if (!sc.valid || sc.tile_log2 != c->tune.tile_log2 || sc.threads != c->tune.threads ||
         sc.ctas != c->tune.ctas_per_sm || sc.smem != want_smem) {
         if (c->capturing) return fail(BNX_E_STATE, "sieve launch shape unknown during capture");
         const int thr = (int)c->tune.threads;
         const size_t smem_b = want_smem;
         int occ = 0;
-        int e = sieve_occupancy(mode, thr, smem_b, &occ);
+        int e = lg ? sieve_log_occupancy(mode, thr, smem_b, &occ) : sieve_occupancy(mode, thr, smem_b, &occ);
         if (e != 0) return fail(BNX_E_CUDA, "sieve occupancy query failed: %s", cudaGetErrorString((cudaError_t)e));
         if (occ < 1) return fail(BNX_E_ARG, "sieve kernel does not fit an SM with this tuning");
         const int per = c->tune.ctas_per_sm ? std::min<int>((int)c->tune.ctas_per_sm, occ) : occ;
@@ -309,7 +321,8 @@ int record_pipeline(bnx_ctx *c, int mode, cudaStream_t s, bool timing) {
     CUDA_TRY(cudaMemsetAsync(c->bcnt.p, 0, c->bcnt.bytes, s));
     launch_bucket(P, true, bgrid, s);
     if (timing) CUDA_TRY(cudaEventRecordWithFlags(c->ev_s0, s, c->capturing ? cudaEventRecordExternal : 0));
-    launch_sieve(P, mode, sgrid, sthreads, ssmem, s);
+    if (use_log_tile(c, mode)) launch_sieve_log(P, mode, sgrid, sthreads, ssmem, s);
+    else launch_sieve(P, mode, sgrid, sthreads, ssmem, s);
     if (timing) CUDA_TRY(cudaEventRecordWithFlags(c->ev_s1, s, c->capturing ? cudaEventRecordExternal : 0));
     if (mode == kModeSearch) {
         launch_verify(P, c->n_sm * 4, s);

@@ -1,0 +1,374 @@
+// Log-domain tile sieve for the search and hash modes (the default).
+//
+// The tile holds, per value x, L(x) = the sum of lg(p) over the prime-power
+// strikes at x, where lg(p) = floor(2^16 log2 p) + 1 > 2^16 log2 p.  So L(x) is
+// an upper bound of 2^16 log2 s_odd(x), s_odd(x) being the odd part of
+// x / rad(x).  Strikes are 32-bit shared-memory reductions (no read-modify-write
+// loop: addition commutes, so strikes of different prime powers at one x need
+// no ordering).  Algorithm 1 (Sec. 2.1) still decides which x a prime power
+// touches; only what is recorded there changes.
+//
+// Filter.  With P = s(n)s(n+1) (powers of 2 included), the per-kind necessary
+// conditions need 2P >= n+1 (second kind, and a fortiori the first) or
+// P >= n(n+1)/(2S) (hash search).  If neither n nor n+1 is divisible by 2^M
+// (M = 12), the power of 2 in P is at most 2^(M-2), so
+//   log2 P <= (L(n) + L(n+1)) / 2^16 + M - 2,
+// and n is rejected when that bound falls below the tile's smallest threshold.
+// Every other n (a bound that does not reject, or n, n+1 next to a multiple of
+// 2^M) is a candidate.  A candidate whose exact power of 2 still rejects it is
+// dropped; the rest get exact square parts (exact-division tests by the in-tile
+// primes, plus the segment's bucket entries of the larger primes) and the exact
+// 128-bit conditions.
+#include "bnx_internal.cuh"
+
+namespace bnx {
+
+namespace {
+
+constexpr int kLogBucketCache = 256;
+constexpr uint32_t kHigh2 = 12;
+constexpr int kMaxSmallPrimes = 64;
+
+__device__ __forceinline__ uint32_t ctz64(uint64_t x) { return (uint32_t)(__ffsll((long long)x) - 1); }
+__device__ __forceinline__ uint32_t flog2_64(uint64_t x) { return 63u - (uint32_t)__clzll((long long)x); }
+
+template <bool SEG>
+__device__ __forceinline__ uint32_t find_iv(const IvDev *ivs, uint32_t k, uint64_t x) {
+    uint32_t lo = 0, hi = k;
+    while (hi - lo > 1) {
+        const uint32_t mid = (lo + hi) >> 1;
+        const uint64_t b = SEG ? ivs[mid].seg_base : ivs[mid].chunk_base;
+        if (b <= x) lo = mid;
+        else hi = mid;
+    }
+    return lo;
+}
+
+struct LogLayout {
+    size_t tile, spp, sched, bcache, blg, total;
+};
+
+__host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+__host__ __device__ inline LogLayout log_layout(uint32_t tile_log2, uint32_t nspp, uint32_t nsched) {
+    LogLayout L;
+    L.tile = 0;
+    L.spp = al16((((size_t)1 << tile_log2) + 8) * sizeof(uint32_t));
+    L.sched = L.spp + al16((size_t)4 * (nspp ? nspp : 1) * sizeof(uint32_t));
+    L.bcache = L.sched + al16((size_t)(nsched ? nsched : 1) * sizeof(uint16_t));
+    L.blg = L.bcache + (size_t)kLogBucketCache * sizeof(uint2);
+    L.total = L.blg + (size_t)kLogBucketCache * sizeof(uint32_t);
+    return L;
+}
+
+// lg of a large prime for a bucket hit: 2^16 log2 p rounded up with margin
+// (log2f is within a few ulps; 4 units of 2^-16 cover that and the truncation)
+__device__ __forceinline__ uint32_t lg_large(uint32_t p) {
+    return __float2uint_rd(log2f((float)p) * 65536.0f) + 4u;
+}
+
+struct SmallPrimes {
+    uint32_t n;
+    uint32_t p[kMaxSmallPrimes];
+    unsigned long long inv[kMaxSmallPrimes];  // p^-1 mod 2^64
+    unsigned long long lim[kMaxSmallPrimes];  // floor((2^64 - 1) / p)
+};
+
+// exact odd square part of the value v at offset o of its segment
+__device__ __noinline__ uint64_t sodd_exact(uint64_t v, uint32_t o, const SmallPrimes *sp, uint32_t sqrt_q,
+                                            const uint2 *bc, uint32_t nbc, const uint2 *bent, unsigned long long gb,
+                                            unsigned long long ge) {
+    uint64_t y = v >> ctz64(v);
+    uint64_t s = 1;
+    for (uint32_t t = 0; t < sp->n; t++) {
+        const unsigned long long inv = sp->inv[t], lim = sp->lim[t];
+        if (y * inv <= lim) {  // p | y (exact-division test)
+            y *= inv;
+            while (y * inv <= lim) {
+                y *= inv;
+                s *= sp->p[t];
+            }
+        }
+    }
+    for (uint32_t e = 0; e < nbc; e++)
+        if (bc[e].x == o && bc[e].y > sqrt_q) s *= bc[e].y;
+    for (unsigned long long e = gb; e < ge; e++) {
+        const uint2 h = bent[e];
+        if (h.x == o && h.y > sqrt_q) s *= h.y;
+    }
+    return s;
+}
+
+// exact per-kind decision from the odd square parts of n and n+1
+__device__ __noinline__ uint32_t exact_kinds_log(uint64_t n, uint64_t s0, uint64_t s1, uint32_t kinds, int mode,
+                                                 uint64_t hash_S, uint64_t *pa, uint64_t *pb) {
+    const uint32_t t0 = ctz64(n), t1 = ctz64(n + 1);
+    const uint64_t sn = s0 << (t0 ? t0 - 1 : 0);
+    const uint64_t sn1 = s1 << (t1 ? t1 - 1 : 0);
+    const uint64_t a = n / sn, b = (n + 1) / sn1;
+    *pa = a;
+    *pb = b;
+    const unsigned __int128 ab = (unsigned __int128)a * b;
+    if (mode == kModeHash) return ab <= (unsigned __int128)2 * hash_S ? 3u : 0u;
+    uint32_t r = 0;
+    if ((kinds & 1) && ab <= (unsigned __int128)(n - 1)) r |= 1;
+    if ((kinds & 2) && ab <= (unsigned __int128)2 * n) {
+        const uint64_t abl = (uint64_t)ab;
+        const uint64_t jlo = (n + 2 + abl - 1) / abl, jhi = (2 * n) / abl;
+        if (jlo <= jhi) r |= 2;
+    }
+    return r;
+}
+
+template <int NT>
+struct LogMinBlocks {
+    static constexpr int value = NT <= 128 ? 8 : NT <= 256 ? 6 : NT <= 512 ? 3 : 1;
+};
+
+template <int MODE, int NT>
+__global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan P) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    const uint32_t tile_log2 = P.tile_log2;
+    const uint32_t LT = 1u << tile_log2;
+    const uint32_t nspp = P.n_spp;
+    const LogLayout lay = log_layout(tile_log2, nspp, P.n_sched);
+    uint32_t *tile = reinterpret_cast<uint32_t *>(smem_raw + lay.tile);
+    uint32_t *sq = reinterpret_cast<uint32_t *>(smem_raw + lay.spp);
+    uint32_t *slg = sq + nspp;
+    uint32_t *soff = slg + nspp;
+    uint32_t *slmod = soff + nspp;
+    uint16_t *sched = reinterpret_cast<uint16_t *>(smem_raw + lay.sched);
+    uint2 *bcache = reinterpret_cast<uint2 *>(smem_raw + lay.bcache);
+    uint32_t *blg = reinterpret_cast<uint32_t *>(smem_raw + lay.blg);
+    __shared__ SmallPrimes sprimes;
+    __shared__ unsigned long long s_seg;
+    __shared__ uint32_t s_iv, s_nsched;
+
+    const uint32_t tid = threadIdx.x;
+    const uint32_t lane = tid & 31, warp = tid >> 5;
+    constexpr uint32_t nwarps = NT / 32;
+    const uint32_t k = *P.n_iv;
+    const unsigned long long total_segs = P.ctr->total_segs;
+
+    for (uint32_t j = tid; j < nspp; j += NT) {
+        const SmallPP e = P.spp[j];
+        sq[j] = e.q;
+        slg[j] = e.lg;
+        slmod[j] = LT % e.q;
+    }
+    if (tid == 0) {
+        // distinct in-tile primes (their square is an in-tile prime power)
+        uint32_t c = 0;
+        for (uint32_t j = 0; j < nspp && c < kMaxSmallPrimes; j++)
+            if (P.spp[j].k == 2) sprimes.p[c++] = P.spp[j].p;
+        sprimes.n = c;
+    }
+    __syncthreads();
+    for (uint32_t t = tid; t < sprimes.n; t += NT) {
+        const unsigned long long p = sprimes.p[t];
+        unsigned long long inv = p;  // Newton: each step doubles the correct low bits
+        for (int it = 0; it < 6; it++) inv *= 2ull - p * inv;
+        sprimes.inv[t] = inv;
+        sprimes.lim[t] = ~0ull / p;
+    }
+    if (warp == 0) {
+        constexpr int kPer = kMaxSpp / 32;
+        uint32_t v[kPer];
+        uint32_t sum = 0;
+#pragma unroll
+        for (int u = 0; u < kPer; u++) {
+            const uint32_t j = lane * kPer + u;
+            v[u] = j < nspp ? (LT / sq[j] + 1 + 31) / 32 : 0;
+            sum += v[u];
+        }
+        uint32_t inc = sum;
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t x = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= (uint32_t)o) inc += x;
+        }
+        uint32_t run = inc - sum;
+#pragma unroll
+        for (int u = 0; u < kPer; u++) {
+            const uint32_t j = lane * kPer + u;
+            for (uint32_t c = 0; c < v[u]; c++)
+                if (run + c < P.n_sched) sched[run + c] = (uint16_t)(j | (c << 8));
+            run += v[u];
+        }
+        if (lane == 31) s_nsched = inc < P.n_sched ? inc : P.n_sched;
+    }
+
+    for (;;) {
+        __syncthreads();
+        if (tid == 0) {
+            s_seg = atomicAdd(&P.ctr->queue_head, 1ull);
+            s_iv = s_seg < total_segs ? find_iv<true>(P.ivs, k, s_seg) : 0;
+        }
+        __syncthreads();
+        const unsigned long long seg = s_seg;
+        if (seg >= total_segs) break;
+        const IvDev iv = P.ivs[s_iv];
+        const uint64_t seg_lo = iv.lo + ((seg - iv.seg_base) << P.seg_log2);
+        const uint64_t rem = iv.hi - seg_lo;
+        const uint32_t seg_len = rem < (1ull << P.seg_log2) ? (uint32_t)rem : (1u << P.seg_log2);
+        const unsigned long long b0 = P.boff[seg], b1 = P.boff[seg + 1];
+        const uint32_t nbc =
+            (uint32_t)((b1 - b0) < (unsigned long long)kLogBucketCache ? (b1 - b0) : kLogBucketCache);
+        for (uint32_t j = tid; j < nspp; j += NT) {
+            const uint32_t q = sq[j];
+            const uint32_t r = (uint32_t)(seg_lo % q);
+            soff[j] = r ? q - r : 0;
+        }
+        for (uint32_t e = tid; e < nbc; e += NT) {
+            const uint2 h = P.bent[b0 + e];
+            bcache[e] = h;
+            blg[e] = lg_large(h.y);
+        }
+        const uint32_t nsched = s_nsched;
+        const uint32_t kinds = iv.kinds;
+
+        for (uint32_t t0 = 0; t0 < seg_len; t0 += LT) {
+            const uint32_t tl = (seg_len - t0) < LT ? (seg_len - t0) : LT;
+            const uint64_t t_lo = seg_lo + t0;
+            // fixed-point threshold of L(n) + L(n+1) below which n is rejected
+            int64_t T;
+            int lthr;  // integer log2 bound for the exact power-of-2 check
+            if (MODE == kModeSearch) {
+                lthr = (int)flog2_64(t_lo + 1) - 1;  // need log2 P >= log2(n+1) - 1
+            } else {
+                const uint64_t S2 = 2 * P.hash_S;
+                const int clog = (int)flog2_64(S2) + ((S2 & (S2 - 1)) ? 1 : 0);
+                lthr = (int)flog2_64(t_lo) + (int)flog2_64(t_lo + 1) - clog;  // need log2 P >= log2(n(n+1)/2S)
+            }
+            T = ((int64_t)lthr - (int64_t)(kHigh2 - 2)) * 65536;
+            const bool all_cand = T <= 0;
+            const uint32_t T32 = all_cand ? 0u : (uint32_t)T;
+            __syncthreads();
+            {
+                uint4 *t4 = reinterpret_cast<uint4 *>(tile);
+                const uint4 z = make_uint4(0, 0, 0, 0);
+                for (uint32_t i = tid; i <= ((tl + 4) >> 2); i += NT) t4[i] = z;
+            }
+            __syncthreads();
+            for (uint32_t g = warp; g < nsched; g += nwarps) {
+                const uint32_t e = sched[g];
+                const uint32_t j = e & 255u;
+                const uint32_t x = soff[j] + (((e >> 8) << 5) + lane) * sq[j];
+                if (x <= tl) atomicAdd(&tile[x], slg[j]);
+            }
+            for (uint32_t e = tid; e < nbc; e += NT) {
+                const uint2 h = bcache[e];
+                if (h.x >= t0 && h.x <= t0 + tl) atomicAdd(&tile[h.x - t0], blg[e]);
+            }
+            for (unsigned long long e = b0 + kLogBucketCache + tid; e < b1; e += NT) {
+                const uint2 h = P.bent[e];
+                if (h.x >= t0 && h.x <= t0 + tl) atomicAdd(&tile[h.x - t0], lg_large(h.y));
+            }
+            __syncthreads();
+            for (uint32_t j = tid; j < nspp; j += NT) {
+                const uint32_t off = soff[j], lm = slmod[j];
+                soff[j] = off >= lm ? off - lm : off + sq[j] - lm;
+            }
+            // epilogue: four consecutive n per thread
+            constexpr uint32_t M2 = 1u << kHigh2;
+            const uint32_t ngroups = (tl + 3) >> 2;
+            const uint4 *t4 = reinterpret_cast<const uint4 *>(tile);
+            for (uint32_t base = 0; base < ngroups; base += NT) {
+                const uint32_t g = base + tid;
+                bool cand = false;
+                if (g < ngroups) {
+                    const uint4 v = t4[g];
+                    const uint32_t w = tile[4 * g + 4];
+                    const uint32_t mx = max(max(v.x + v.y, v.y + v.z), max(v.z + v.w, v.w + w));
+                    // does [n0, n0 + 4] hold a multiple of 2^M?
+                    const bool hi2 = (((uint32_t)(t_lo + 4 * g) + 4u) & (M2 - 1)) <= 4u;
+                    cand = all_cand || mx >= T32 || hi2;
+                }
+                if (!__any_sync(0xffffffffu, cand)) continue;
+#pragma unroll 1
+                for (uint32_t u = 0; u < 4; u++) {
+                    const uint32_t i = 4 * g + u;
+                    uint32_t kk = 0;
+                    uint64_t n = 0, a = 0, b = 0;
+                    if (cand && i < tl) {
+                        n = t_lo + i;
+                        const uint32_t e2 = ctz64(n + (n & 1)) - 1;  // power of 2 in P
+                        // log2 P <= sums/2^16 + e2; drop n when that is below the threshold
+                        const int64_t ub = (int64_t)(tile[i] + tile[i + 1]) + (int64_t)e2 * 65536;
+                        int need;
+                        if (MODE == kModeSearch) need = (int)flog2_64(n + 1) - 1;
+                        else {
+                            const uint64_t S2 = 2 * P.hash_S;
+                            need = (int)flog2_64(n) + (int)flog2_64(n + 1) - (int)flog2_64(S2) -
+                                   ((S2 & (S2 - 1)) ? 1 : 0);
+                        }
+                        if (ub >= (int64_t)need * 65536) {
+                            const uint64_t s0 = sodd_exact(n, t0 + i, &sprimes, P.sqrt_q, bcache, nbc, P.bent,
+                                                           b0 + kLogBucketCache, b1);
+                            const uint64_t s1 = sodd_exact(n + 1, t0 + i + 1, &sprimes, P.sqrt_q, bcache, nbc,
+                                                           P.bent, b0 + kLogBucketCache, b1);
+                            kk = exact_kinds_log(n, s0, s1, kinds, MODE, P.hash_S, &a, &b);
+                        }
+                    }
+                    const uint32_t m = __ballot_sync(0xffffffffu, kk != 0);
+                    if (m) {
+                        unsigned long long wbase = 0;
+                        if (lane == 0) wbase = atomicAdd(&P.ctr->n_surv, (unsigned long long)__popc(m));
+                        wbase = __shfl_sync(0xffffffffu, wbase, 0);
+                        if (kk) {
+                            const unsigned long long at = wbase + __popc(m & ((1u << lane) - 1));
+                            if (at < P.surv_cap) {
+                                Survivor sv;
+                                sv.n = n;
+                                sv.a = a;
+                                sv.b = b;
+                                sv.kinds = kk;
+                                sv.iv = s_iv;
+                                P.surv[at] = sv;
+                            } else {
+                                atomicOr(&P.ctr->err, kErrSurvOverflow);
+                            }
+                            if (MODE == kModeSearch) {
+                                if (kk & 1) atomicAdd(&P.ctr->surv1, 1ull);
+                                if (kk & 2) atomicAdd(&P.ctr->surv2, 1ull);
+                            }
+                        }
+                    }
+                }
+            }
+        }
+    }
+}
+
+template <int MODE>
+const void *log_fn_t(int threads) {
+    switch (threads) {
+        case 128: return (const void *)k_sieve_log<MODE, 128>;
+        case 256: return (const void *)k_sieve_log<MODE, 256>;
+        case 512: return (const void *)k_sieve_log<MODE, 512>;
+        default: return (const void *)k_sieve_log<MODE, 1024>;
+    }
+}
+
+const void *log_fn(int mode, int threads) {
+    return mode == kModeHash ? log_fn_t<kModeHash>(threads) : log_fn_t<kModeSearch>(threads);
+}
+
+}  // namespace
+
+size_t sieve_log_smem_bytes(uint32_t tile_log2, uint32_t nspp, uint32_t nsched) {
+    return log_layout(tile_log2, nspp, nsched).total;
+}
+
+int sieve_log_occupancy(int mode, int threads, size_t smem, int *ctas_per_sm) {
+    const void *fn = log_fn(mode, threads);
+    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return (int)e;
+    return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, fn, threads, smem);
+}
+
+void launch_sieve_log(const Plan &P, int mode, int grid, int threads, size_t smem, cudaStream_t s) {
+    void *args[] = {(void *)&P};
+    cudaLaunchKernel(log_fn(mode, threads), dim3(grid), dim3(threads), args, smem, s);
+}
+
+}  // namespace bnx

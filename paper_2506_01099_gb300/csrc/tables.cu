@@ -92,11 +92,15 @@ __global__ void k_build_pp(const uint32_t *primes, uint32_t np, uint64_t max_hi,
         uint64_t p = primes[i];
         if (p == 2) continue;  // the prime 2 is handled by counting trailing zeros
         if (p * p > max_hi) break;
-        for (uint64_t q = p * p;; q *= p) {
+        const uint32_t lg = (uint32_t)floor(log2((double)p) * (double)(1u << kLogFrac)) + 1u;
+        uint32_t e = 2;
+        for (uint64_t q = p * p;; q *= p, e++) {
             if (q <= q_small) {
                 if (ns < kMaxSpp) {
                     spp[ns].q = (uint32_t)q;
                     spp[ns].p = (uint32_t)p;
+                    spp[ns].lg = lg;
+                    spp[ns].k = e;
                 }
                 ns++;
             } else {

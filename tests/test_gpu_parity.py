@@ -79,7 +79,9 @@ def test_rad_segment_large_sampled(ctx, orc):
 
 @pytest.mark.parametrize("tune", [dict(tile_log2=12, seg_tiles=1, small_q_log2=10),
                                   dict(tile_log2=14, seg_tiles=4, threads=1024, small_q_log2=16),
-                                  dict(tile_log2=11, seg_tiles=16, threads=256, small_q_log2=8)])
+                                  dict(tile_log2=11, seg_tiles=16, threads=256, small_q_log2=8),
+                                  dict(exact_tile=1),
+                                  dict(exact_tile=1, tile_log2=12, threads=256, small_q_log2=12)])
 def test_tunings_agree(B, orc, tune):
     with B.Context(0, max_hi=1 << 41) as c:
         c.set_tune(**tune)
@@ -87,7 +89,11 @@ def test_tunings_agree(B, orc, tune):
             rad, _ = gpu_rad(c, lo, length)
             assert np.array_equal(rad, orc.rad_td_array(lo, length))
         assert c.search(1, 1 << 20) == theorem1_pairs(1, 1 << 20)
+        st = c.stats()
+        assert (st["survivors1"], st["survivors2"]) == orc.filter_counts(1, 1 << 20)
         assert c.search(2**40 - 2**21 - 8, 2**40 + 2**21 + 8) == theorem1_pairs(2**40 - 2**21 - 8, 2**40 + 2**21 + 8)
+        assert c.search_hash(1 << 20) == orc.pairs_sort(1 << 20)
+        assert c.stats()["hash_keys"] == orc.hash_keys(1 << 20)
 
 
 def test_search_c1_full(ctx, orc):
