@@ -44,22 +44,18 @@ __device__ __forceinline__ uint32_t find_iv(const IvDev *ivs, uint32_t k, uint64
     return lo;
 }
 
-// Shared memory of one CTA: three tile buffers (strikes of tile t, the
-// epilogue of tile t-1 and the zeroing of tile t+1 run in the same phase, so a
-// tile costs one barrier), the in-tile prime powers (q, lg, L_tile mod q, warp
-// chunks per q, two offset buffers), and the segment's bucket entries.
 struct LogLayout {
-    size_t buf_words, spp, bcache, blg, total;
+    size_t tile, spp, sched, bcache, blg, total;
 };
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
 __host__ __device__ inline LogLayout log_layout(uint32_t tile_log2, uint32_t nspp, uint32_t nsched) {
-    (void)nsched;
     LogLayout L;
-    L.buf_words = ((size_t)1 << tile_log2) + 8;  // multiple of 4: every buffer stays 16-byte aligned
-    L.spp = al16(3 * L.buf_words * sizeof(uint32_t));
-    L.bcache = L.spp + al16((size_t)6 * (nspp ? nspp : 1) * sizeof(uint32_t));
+    L.tile = 0;
+    L.spp = al16((((size_t)1 << tile_log2) + 8) * sizeof(uint32_t));
+    L.sched = L.spp + al16((size_t)4 * (nspp ? nspp : 1) * sizeof(uint32_t));
+    L.bcache = L.sched + al16((size_t)(nsched ? nsched : 1) * sizeof(uint16_t));
     L.blg = L.bcache + (size_t)kLogBucketCache * sizeof(uint2);
     L.total = L.blg + (size_t)kLogBucketCache * sizeof(uint32_t);
     return L;
@@ -125,29 +121,28 @@ __device__ __noinline__ uint32_t exact_kinds_log(uint64_t n, uint64_t s0, uint64
 }
 
 template <int NT>
-struct LogMinBlocks {  // three tile buffers: at most 2048 threads' worth of CTAs fit an SM anyway
-    static constexpr int value = NT <= 128 ? 8 : NT <= 256 ? 4 : NT <= 512 ? 2 : 1;
+struct LogMinBlocks {
+    static constexpr int value = NT <= 128 ? 8 : NT <= 256 ? 6 : NT <= 512 ? 3 : 1;
 };
 
 template <int MODE, int NT>
 __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    const uint32_t LT = 1u << P.tile_log2;
+    const uint32_t tile_log2 = P.tile_log2;
+    const uint32_t LT = 1u << tile_log2;
     const uint32_t nspp = P.n_spp;
-    const LogLayout lay = log_layout(P.tile_log2, nspp, P.n_sched);
-    uint32_t *bufs = reinterpret_cast<uint32_t *>(smem_raw);
-    const uint32_t bw = (uint32_t)lay.buf_words;
+    const LogLayout lay = log_layout(tile_log2, nspp, P.n_sched);
+    uint32_t *tile = reinterpret_cast<uint32_t *>(smem_raw + lay.tile);
     uint32_t *sq = reinterpret_cast<uint32_t *>(smem_raw + lay.spp);
     uint32_t *slg = sq + nspp;
-    uint32_t *slmod = slg + nspp;
-    uint32_t *sc = slmod + nspp;    // warp-chunks of q in a tile
-    uint32_t *soff = sc + nspp;     // two offset buffers: soff[par * nspp + j]
+    uint32_t *soff = slg + nspp;
+    uint32_t *slmod = soff + nspp;
+    uint16_t *sched = reinterpret_cast<uint16_t *>(smem_raw + lay.sched);
     uint2 *bcache = reinterpret_cast<uint2 *>(smem_raw + lay.bcache);
     uint32_t *blg = reinterpret_cast<uint32_t *>(smem_raw + lay.blg);
     __shared__ SmallPrimes sprimes;
     __shared__ unsigned long long s_seg;
-    __shared__ uint32_t s_iv;
-    __shared__ uint32_t w_j0[32], w_c0[32], w_cnt[32];  // static strike range of each warp
+    __shared__ uint32_t s_iv, s_nsched;
 
     const uint32_t tid = threadIdx.x;
     const uint32_t lane = tid & 31, warp = tid >> 5;
@@ -160,10 +155,10 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
         sq[j] = e.q;
         slg[j] = e.lg;
         slmod[j] = LT % e.q;
-        sc[j] = (LT / e.q + 1 + 31) / 32;  // a tile holds at most floor(L_tile/q)+1 multiples of q
     }
     if (tid == 0) {
-        uint32_t c = 0;  // distinct in-tile primes: their square is an in-tile prime power
+        // distinct in-tile primes (their square is an in-tile prime power)
+        uint32_t c = 0;
         for (uint32_t j = 0; j < nspp && c < kMaxSmallPrimes; j++)
             if (P.spp[j].k == 2) sprimes.p[c++] = P.spp[j].p;
         sprimes.n = c;
@@ -177,15 +172,13 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
         sprimes.lim[t] = ~0ull / p;
     }
     if (warp == 0) {
-        // all warp-chunks (j, c) in j-major order, split into nwarps equal ranges
-        uint32_t *pre = soff;  // scratch until the first segment
         constexpr int kPer = kMaxSpp / 32;
         uint32_t v[kPer];
         uint32_t sum = 0;
 #pragma unroll
         for (int u = 0; u < kPer; u++) {
             const uint32_t j = lane * kPer + u;
-            v[u] = j < nspp ? sc[j] : 0;
+            v[u] = j < nspp ? (LT / sq[j] + 1 + 31) / 32 : 0;
             sum += v[u];
         }
         uint32_t inc = sum;
@@ -197,24 +190,11 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
 #pragma unroll
         for (int u = 0; u < kPer; u++) {
             const uint32_t j = lane * kPer + u;
-            if (j < nspp) pre[j] = run;
+            for (uint32_t c = 0; c < v[u]; c++)
+                if (run + c < P.n_sched) sched[run + c] = (uint16_t)(j | (c << 8));
             run += v[u];
         }
-        const uint32_t C = __shfl_sync(0xffffffffu, inc, 31);
-        __syncwarp();
-        if (lane < nwarps) {
-            const uint32_t g0 = (uint32_t)((unsigned long long)C * lane / nwarps);
-            const uint32_t g1 = (uint32_t)((unsigned long long)C * (lane + 1) / nwarps);
-            uint32_t lo = 0, hi = nspp;  // last j with pre[j] <= g0
-            while (hi - lo > 1) {
-                const uint32_t mid = (lo + hi) >> 1;
-                if (pre[mid] <= g0) lo = mid;
-                else hi = mid;
-            }
-            w_j0[lane] = lo;
-            w_c0[lane] = g0 - pre[lo];
-            w_cnt[lane] = g1 - g0;
-        }
+        if (lane == 31) s_nsched = inc < P.n_sched ? inc : P.n_sched;
     }
 
     for (;;) {
@@ -230,7 +210,6 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
         const uint64_t seg_lo = iv.lo + ((seg - iv.seg_base) << P.seg_log2);
         const uint64_t rem = iv.hi - seg_lo;
         const uint32_t seg_len = rem < (1ull << P.seg_log2) ? (uint32_t)rem : (1u << P.seg_log2);
-        const uint32_t ntiles = (seg_len + LT - 1) >> P.tile_log2;
         const unsigned long long b0 = P.boff[seg], b1 = P.boff[seg + 1];
         const uint32_t nbc =
             (uint32_t)((b1 - b0) < (unsigned long long)kLogBucketCache ? (b1 - b0) : kLogBucketCache);
@@ -244,142 +223,118 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
             bcache[e] = h;
             blg[e] = lg_large(h.y);
         }
-        {
-            const uint32_t tl0 = seg_len < LT ? seg_len : LT;
-            uint4 *z4 = reinterpret_cast<uint4 *>(bufs);
-            for (uint32_t i = tid; i < ((tl0 + 8 + 3) >> 2); i += NT) z4[i] = make_uint4(0, 0, 0, 0);
-        }
+        const uint32_t nsched = s_nsched;
         const uint32_t kinds = iv.kinds;
-        __syncthreads();
 
-        for (uint32_t st = 0; st <= ntiles; st++) {
-            // ---- strikes of tile st
-            if (st < ntiles) {
-                const uint32_t t0 = st * LT;
-                const uint32_t tl = (seg_len - t0) < LT ? (seg_len - t0) : LT;
-                uint32_t *B = bufs + (st % 3) * bw;
-                const uint32_t *so = soff + (st & 1) * nspp;
-                uint32_t j = w_j0[warp], c = w_c0[warp], left = w_cnt[warp];
-                while (left) {
-                    const uint32_t q = sq[j], lg = slg[j], cj = sc[j];
-                    const uint32_t base = so[j] + lane * q, step = 32 * q;
-                    uint32_t nh = cj - c;
-                    if (nh > left) nh = left;
-                    uint32_t x = base + c * step;
-                    for (uint32_t r = 0; r < nh; r++, x += step)
-                        if (x <= tl) atomicAdd(&B[x], lg);
-                    left -= nh;
-                    j++;
-                    c = 0;
-                }
-                for (uint32_t e = tid; e < nbc; e += NT) {
-                    const uint2 h = bcache[e];
-                    if (h.x >= t0 && h.x <= t0 + tl) atomicAdd(&B[h.x - t0], blg[e]);
-                }
-                for (unsigned long long e = b0 + kLogBucketCache + tid; e < b1; e += NT) {
-                    const uint2 h = P.bent[e];
-                    if (h.x >= t0 && h.x <= t0 + tl) atomicAdd(&B[h.x - t0], lg_large(h.y));
-                }
-                uint32_t *sn = soff + ((st + 1) & 1) * nspp;
-                for (uint32_t jj = tid; jj < nspp; jj += NT) {  // offsets of the next tile: (off - L_tile) mod q
-                    const uint32_t off = so[jj], lm = slmod[jj];
-                    sn[jj] = off >= lm ? off - lm : off + sq[jj] - lm;
-                }
+        for (uint32_t t0 = 0; t0 < seg_len; t0 += LT) {
+            const uint32_t tl = (seg_len - t0) < LT ? (seg_len - t0) : LT;
+            const uint64_t t_lo = seg_lo + t0;
+            // fixed-point threshold of L(n) + L(n+1) below which n is rejected
+            int64_t T;
+            int lthr;  // integer log2 bound for the exact power-of-2 check
+            if (MODE == kModeSearch) {
+                lthr = (int)flog2_64(t_lo + 1) - 1;  // need log2 P >= log2(n+1) - 1
+            } else {
+                const uint64_t S2 = 2 * P.hash_S;
+                const int clog = (int)flog2_64(S2) + ((S2 & (S2 - 1)) ? 1 : 0);
+                lthr = (int)flog2_64(t_lo) + (int)flog2_64(t_lo + 1) - clog;  // need log2 P >= log2(n(n+1)/2S)
             }
-            // ---- epilogue of tile st - 1
-            if (st >= 1) {
-                const uint32_t et = st - 1;
-                const uint32_t t0 = et * LT;
-                const uint32_t tl = (seg_len - t0) < LT ? (seg_len - t0) : LT;
-                const uint64_t t_lo = seg_lo + t0;
-                const uint32_t *B = bufs + (et % 3) * bw;
-                int lthr;  // integer log2 that P = s(n)s(n+1) must reach at the tile's smallest n
-                if (MODE == kModeSearch) {
-                    lthr = (int)flog2_64(t_lo + 1) - 1;
-                } else {
-                    const uint64_t S2 = 2 * P.hash_S;
-                    const int clog = (int)flog2_64(S2) + ((S2 & (S2 - 1)) ? 1 : 0);
-                    lthr = (int)flog2_64(t_lo) + (int)flog2_64(t_lo + 1) - clog;
-                }
-                const int64_t T = ((int64_t)lthr - (int64_t)(kHigh2 - 2)) * 65536;
-                const bool all_cand = T <= 0;
-                const uint32_t T32 = all_cand ? 0u : (uint32_t)T;
-                constexpr uint32_t M2 = 1u << kHigh2;
-                const uint32_t ngroups = (tl + 3) >> 2;
-                const uint4 *t4 = reinterpret_cast<const uint4 *>(B);
-                for (uint32_t gb = 0; gb < ngroups; gb += NT) {
-                    const uint32_t g = gb + tid;
-                    const uint4 v = g <= ngroups ? t4[g] : make_uint4(0, 0, 0, 0);
-                    uint32_t w = __shfl_down_sync(0xffffffffu, v.x, 1);  // first word of the next group
-                    if (lane == 31) w = g < ngroups ? B[4 * g + 4] : 0u;
-                    bool cand = false;
-                    if (g < ngroups) {
-                        const uint32_t mx = max(max(v.x + v.y, v.y + v.z), max(v.z + v.w, v.w + w));
-                        // does [n0, n0 + 4] hold a multiple of 2^M?
-                        const bool hi2 = (((uint32_t)(t_lo + 4 * g) + 4u) & (M2 - 1)) <= 4u;
-                        cand = all_cand || mx >= T32 || hi2;
-                    }
-                    if (!__any_sync(0xffffffffu, cand)) continue;
-#pragma unroll 1
-                    for (uint32_t u = 0; u < 4; u++) {
-                        const uint32_t i = 4 * g + u;
-                        uint32_t kk = 0;
-                        uint64_t n = 0, a = 0, b = 0;
-                        if (cand && i < tl) {
-                            n = t_lo + i;
-                            const uint32_t e2 = ctz64(n + (n & 1)) - 1;  // power of 2 in P
-                            const int64_t ub = (int64_t)(B[i] + B[i + 1]) + (int64_t)e2 * 65536;
-                            int need;  // log2 P <= ub / 2^16 must reach it
-                            if (MODE == kModeSearch) {
-                                need = (int)flog2_64(n + 1) - 1;
-                            } else {
-                                const uint64_t S2 = 2 * P.hash_S;
-                                need = (int)flog2_64(n) + (int)flog2_64(n + 1) - (int)flog2_64(S2) -
-                                       ((S2 & (S2 - 1)) ? 1 : 0);
-                            }
-                            if (ub >= (int64_t)need * 65536) {
-                                const uint64_t s0 = sodd_exact(n, t0 + i, &sprimes, P.sqrt_q, bcache, nbc, P.bent,
-                                                               b0 + kLogBucketCache, b1);
-                                const uint64_t s1 = sodd_exact(n + 1, t0 + i + 1, &sprimes, P.sqrt_q, bcache, nbc,
-                                                               P.bent, b0 + kLogBucketCache, b1);
-                                kk = exact_kinds_log(n, s0, s1, kinds, MODE, P.hash_S, &a, &b);
-                            }
-                        }
-                        const uint32_t m = __ballot_sync(0xffffffffu, kk != 0);  // warp-ballot compaction
-                        if (m) {
-                            unsigned long long wbase = 0;
-                            if (lane == 0) wbase = atomicAdd(&P.ctr->n_surv, (unsigned long long)__popc(m));
-                            wbase = __shfl_sync(0xffffffffu, wbase, 0);
-                            if (kk) {
-                                const unsigned long long at = wbase + __popc(m & ((1u << lane) - 1));
-                                if (at < P.surv_cap) {
-                                    Survivor sv;
-                                    sv.n = n;
-                                    sv.a = a;
-                                    sv.b = b;
-                                    sv.kinds = kk;
-                                    sv.iv = s_iv;
-                                    P.surv[at] = sv;
-                                } else {
-                                    atomicOr(&P.ctr->err, kErrSurvOverflow);
-                                }
-                                if (MODE == kModeSearch) {
-                                    if (kk & 1) atomicAdd(&P.ctr->surv1, 1ull);
-                                    if (kk & 2) atomicAdd(&P.ctr->surv2, 1ull);
-                                }
-                            }
-                        }
-                    }
-                }
-            }
-            // ---- zero the buffer of tile st + 1
-            if (st + 1 < ntiles) {
-                const uint32_t t0 = (st + 1) * LT;
-                const uint32_t tl = (seg_len - t0) < LT ? (seg_len - t0) : LT;
-                uint4 *z4 = reinterpret_cast<uint4 *>(bufs + ((st + 1) % 3) * bw);
-                for (uint32_t i = tid; i < ((tl + 8 + 3) >> 2); i += NT) z4[i] = make_uint4(0, 0, 0, 0);
+            T = ((int64_t)lthr - (int64_t)(kHigh2 - 2)) * 65536;
+            const bool all_cand = T <= 0;
+            const uint32_t T32 = all_cand ? 0u : (uint32_t)T;
+            __syncthreads();
+            {
+                uint4 *t4 = reinterpret_cast<uint4 *>(tile);
+                const uint4 z = make_uint4(0, 0, 0, 0);
+                for (uint32_t i = tid; i <= ((tl + 4) >> 2); i += NT) t4[i] = z;
             }
             __syncthreads();
+            for (uint32_t g = warp; g < nsched; g += nwarps) {
+                const uint32_t e = sched[g];
+                const uint32_t j = e & 255u;
+                const uint32_t x = soff[j] + (((e >> 8) << 5) + lane) * sq[j];
+                if (x <= tl) atomicAdd(&tile[x], slg[j]);
+            }
+            for (uint32_t e = tid; e < nbc; e += NT) {
+                const uint2 h = bcache[e];
+                if (h.x >= t0 && h.x <= t0 + tl) atomicAdd(&tile[h.x - t0], blg[e]);
+            }
+            for (unsigned long long e = b0 + kLogBucketCache + tid; e < b1; e += NT) {
+                const uint2 h = P.bent[e];
+                if (h.x >= t0 && h.x <= t0 + tl) atomicAdd(&tile[h.x - t0], lg_large(h.y));
+            }
+            __syncthreads();
+            for (uint32_t j = tid; j < nspp; j += NT) {
+                const uint32_t off = soff[j], lm = slmod[j];
+                soff[j] = off >= lm ? off - lm : off + sq[j] - lm;
+            }
+            // epilogue: four consecutive n per thread
+            constexpr uint32_t M2 = 1u << kHigh2;
+            const uint32_t ngroups = (tl + 3) >> 2;
+            const uint4 *t4 = reinterpret_cast<const uint4 *>(tile);
+            for (uint32_t base = 0; base < ngroups; base += NT) {
+                const uint32_t g = base + tid;
+                bool cand = false;
+                if (g < ngroups) {
+                    const uint4 v = t4[g];
+                    const uint32_t w = tile[4 * g + 4];
+                    const uint32_t mx = max(max(v.x + v.y, v.y + v.z), max(v.z + v.w, v.w + w));
+                    // does [n0, n0 + 4] hold a multiple of 2^M?
+                    const bool hi2 = (((uint32_t)(t_lo + 4 * g) + 4u) & (M2 - 1)) <= 4u;
+                    cand = all_cand || mx >= T32 || hi2;
+                }
+                if (!__any_sync(0xffffffffu, cand)) continue;
+#pragma unroll 1
+                for (uint32_t u = 0; u < 4; u++) {
+                    const uint32_t i = 4 * g + u;
+                    uint32_t kk = 0;
+                    uint64_t n = 0, a = 0, b = 0;
+                    if (cand && i < tl) {
+                        n = t_lo + i;
+                        const uint32_t e2 = ctz64(n + (n & 1)) - 1;  // power of 2 in P
+                        // log2 P <= sums/2^16 + e2; drop n when that is below the threshold
+                        const int64_t ub = (int64_t)(tile[i] + tile[i + 1]) + (int64_t)e2 * 65536;
+                        int need;
+                        if (MODE == kModeSearch) need = (int)flog2_64(n + 1) - 1;
+                        else {
+                            const uint64_t S2 = 2 * P.hash_S;
+                            need = (int)flog2_64(n) + (int)flog2_64(n + 1) - (int)flog2_64(S2) -
+                                   ((S2 & (S2 - 1)) ? 1 : 0);
+                        }
+                        if (ub >= (int64_t)need * 65536) {
+                            const uint64_t s0 = sodd_exact(n, t0 + i, &sprimes, P.sqrt_q, bcache, nbc, P.bent,
+                                                           b0 + kLogBucketCache, b1);
+                            const uint64_t s1 = sodd_exact(n + 1, t0 + i + 1, &sprimes, P.sqrt_q, bcache, nbc,
+                                                           P.bent, b0 + kLogBucketCache, b1);
+                            kk = exact_kinds_log(n, s0, s1, kinds, MODE, P.hash_S, &a, &b);
+                        }
+                    }
+                    const uint32_t m = __ballot_sync(0xffffffffu, kk != 0);
+                    if (m) {
+                        unsigned long long wbase = 0;
+                        if (lane == 0) wbase = atomicAdd(&P.ctr->n_surv, (unsigned long long)__popc(m));
+                        wbase = __shfl_sync(0xffffffffu, wbase, 0);
+                        if (kk) {
+                            const unsigned long long at = wbase + __popc(m & ((1u << lane) - 1));
+                            if (at < P.surv_cap) {
+                                Survivor sv;
+                                sv.n = n;
+                                sv.a = a;
+                                sv.b = b;
+                                sv.kinds = kk;
+                                sv.iv = s_iv;
+                                P.surv[at] = sv;
+                            } else {
+                                atomicOr(&P.ctr->err, kErrSurvOverflow);
+                            }
+                            if (MODE == kModeSearch) {
+                                if (kk & 1) atomicAdd(&P.ctr->surv1, 1ull);
+                                if (kk & 2) atomicAdd(&P.ctr->surv2, 1ull);
+                            }
+                        }
+                    }
+                }
+            }
         }
     }
 }
