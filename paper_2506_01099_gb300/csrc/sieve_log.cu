@@ -11,7 +11,7 @@
 // Filter.  With P = s(n)s(n+1) (powers of 2 included), the per-kind necessary
 // conditions need 2P >= n+1 (second kind, and a fortiori the first) or
 // P >= n(n+1)/(2S) (hash search).  If neither n nor n+1 is divisible by 2^M
-// (M = 12), the power of 2 in P is at most 2^(M-2), so
+// (M = 16), the power of 2 in P is at most 2^(M-2), so
 //   log2 P <= (L(n) + L(n+1)) / 2^16 + M - 2,
 // and n is rejected when that bound falls below the tile's smallest threshold.
 // Every other n (a bound that does not reject, or n, n+1 next to a multiple of
@@ -26,7 +26,7 @@ namespace bnx {
 namespace {
 
 constexpr int kLogBucketCache = 256;
-constexpr uint32_t kHigh2 = 12;
+constexpr uint32_t kHigh2 = 16;
 constexpr int kMaxSmallPrimes = 64;
 
 __device__ __forceinline__ uint32_t ctz64(uint64_t x) { return (uint32_t)(__ffsll((long long)x) - 1); }
@@ -121,8 +121,8 @@ __device__ __noinline__ uint32_t exact_kinds_log(uint64_t n, uint64_t s0, uint64
 }
 
 template <int NT>
-struct LogMinBlocks {
-    static constexpr int value = NT <= 128 ? 8 : NT <= 256 ? 6 : NT <= 512 ? 3 : 1;
+struct LogMinBlocks {  // 64 registers per thread at every CTA size
+    static constexpr int value = NT <= 128 ? 8 : NT <= 256 ? 4 : NT <= 512 ? 2 : 1;
 };
 
 template <int MODE, int NT>
@@ -274,29 +274,39 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
             const uint4 *t4 = reinterpret_cast<const uint4 *>(tile);
             for (uint32_t base = 0; base < ngroups; base += NT) {
                 const uint32_t g = base + tid;
-                bool cand = false;
+                uint32_t cm = 0;  // candidates among the group's four n (bit u: n = t_lo + 4g + u)
                 if (g < ngroups) {
                     const uint4 v = t4[g];
                     const uint32_t w = tile[4 * g + 4];
-                    const uint32_t mx = max(max(v.x + v.y, v.y + v.z), max(v.z + v.w, v.w + w));
+                    const uint32_t s0 = v.x + v.y, s1 = v.y + v.z, s2 = v.z + v.w, s3 = v.w + w;
+                    const uint32_t mx = max(max(s0, s1), max(s2, s3));
+                    const uint32_t n0 = (uint32_t)(t_lo + 4 * g);  // low 32 bits suffice modulo 2^M
                     // does [n0, n0 + 4] hold a multiple of 2^M?
-                    const bool hi2 = (((uint32_t)(t_lo + 4 * g) + 4u) & (M2 - 1)) <= 4u;
-                    cand = all_cand || mx >= T32 || hi2;
+                    const bool hi2 = ((n0 + 4u) & (M2 - 1)) <= 4u;
+                    if (all_cand || mx >= T32 || hi2) {
+                        const uint32_t ss[4] = {s0, s1, s2, s3};
+#pragma unroll
+                        for (uint32_t u = 0; u < 4; u++) {
+                            const uint32_t nl = n0 + u;
+                            const bool h = ((nl & (M2 - 1)) == 0) || (((nl + 1) & (M2 - 1)) == 0);
+                            if ((all_cand || ss[u] >= T32 || h) && 4 * g + u < tl) cm |= 1u << u;
+                        }
+                    }
                 }
-                if (!__any_sync(0xffffffffu, cand)) continue;
-#pragma unroll 1
-                for (uint32_t u = 0; u < 4; u++) {
-                    const uint32_t i = 4 * g + u;
+                while (__any_sync(0xffffffffu, cm != 0)) {
                     uint32_t kk = 0;
                     uint64_t n = 0, a = 0, b = 0;
-                    if (cand && i < tl) {
+                    if (cm) {
+                        const uint32_t u = (uint32_t)(__ffs(cm) - 1);
+                        cm &= cm - 1;
+                        const uint32_t i = 4 * g + u;
                         n = t_lo + i;
                         const uint32_t e2 = ctz64(n + (n & 1)) - 1;  // power of 2 in P
-                        // log2 P <= sums/2^16 + e2; drop n when that is below the threshold
                         const int64_t ub = (int64_t)(tile[i] + tile[i + 1]) + (int64_t)e2 * 65536;
-                        int need;
-                        if (MODE == kModeSearch) need = (int)flog2_64(n + 1) - 1;
-                        else {
+                        int need;  // log2 P <= ub / 2^16 must reach it
+                        if (MODE == kModeSearch) {
+                            need = (int)flog2_64(n + 1) - 1;
+                        } else {
                             const uint64_t S2 = 2 * P.hash_S;
                             need = (int)flog2_64(n) + (int)flog2_64(n + 1) - (int)flog2_64(S2) -
                                    ((S2 & (S2 - 1)) ? 1 : 0);
@@ -309,7 +319,7 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
                             kk = exact_kinds_log(n, s0, s1, kinds, MODE, P.hash_S, &a, &b);
                         }
                     }
-                    const uint32_t m = __ballot_sync(0xffffffffu, kk != 0);
+                    const uint32_t m = __ballot_sync(0xffffffffu, kk != 0);  // warp-ballot compaction
                     if (m) {
                         unsigned long long wbase = 0;
                         if (lane == 0) wbase = atomicAdd(&P.ctr->n_surv, (unsigned long long)__popc(m));
