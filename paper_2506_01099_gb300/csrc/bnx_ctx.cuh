@@ -51,7 +51,6 @@ struct bnx_ctx {
     bool own_stream = false;
     int n_sm = 0;
     bnx_tune tune{};
-    uint32_t chunk_log2 = 26;
 
     // device tables
     bnx::DevBuf primes, spp, lpp, tmp_counts;
@@ -93,6 +92,7 @@ struct bnx_ctx {
         while ((1u << l) < tune.seg_tiles) l++;
         return tune.tile_log2 + l;
     }
+    uint32_t chunk_log2() const { return seg_log2() + bnx::kChunkSegsLog2; }
     bool server_running() const { return serving.load(); }
     std::vector<bnx::DevBuf *> all_bufs() {
         return {&primes, &spp,   &lpp,          &tmp_counts, &ivs,  &n_iv,  &ctr,  &bcnt,  &boff,  &bent,

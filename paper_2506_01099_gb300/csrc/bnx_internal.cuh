@@ -34,9 +34,13 @@ struct SmallPP {
 
 struct LargePP {
     uint64_t q;  // p^k
+    uint64_t m;  // floor((2^64 - 1) / q): v mod q by a multiply-high and one correction
     uint32_t p;
     uint32_t pad;
 };
+
+// A bucket-fill chunk is 2^kChunkSegsLog2 whole queue segments.
+constexpr uint32_t kChunkSegsLog2 = 9;
 
 // One interval of a pipeline run.  n-range [lo, hi); sieved values [lo, hi].
 struct IvDev {
@@ -86,8 +90,9 @@ struct Plan {
     uint32_t n_spp;
     uint32_t n_sched;  // length of the static strike schedule
     uint32_t sqrt_q;   // floor(sqrt(Q)): primes above it reach the tile only through buckets
-    const LargePP *lpp;
+    const LargePP *lpp;  // sorted by q
     uint32_t n_lpp;
+    uint32_t n_lpp_dense;  // entries with q <= 2^(chunk_log2 - 8): walked by a whole warp
     uint32_t tile_log2, seg_log2;  // tile 2^tile_log2 integers, queue segment 2^seg_log2
     uint32_t chunk_log2;           // bucket-fill chunk: 2^chunk_log2 sieved values
     uint32_t *bcnt;                // [seg capacity]
@@ -128,6 +133,8 @@ void launch_exclusive_scan_u32(const uint32_t *in, unsigned long long *out, cons
                                uint64_t n_cap, unsigned long long *tmp, uint32_t tmp_cap, cudaStream_t s);
 void launch_build_pp(const uint32_t *primes, uint32_t np, uint64_t max_hi, uint32_t q_small, SmallPP *spp,
                      uint32_t *n_spp, LargePP *lpp, uint32_t *n_lpp, uint64_t lpp_cap, cudaStream_t s);
+// sort lpp[0 .. n_pow2) by q (entries beyond the table hold q = 2^64 - 1)
+void launch_sort_lpp(LargePP *lpp, uint32_t n_valid, uint32_t n_pow2, cudaStream_t s);
 
 // sieve.cu
 void launch_plan(const Plan &P, uint32_t *n_iv_dev, IvDev *ivs, uint64_t max_iv, cudaStream_t s);

@@ -55,9 +55,9 @@ static uint64_t isqrt64(uint64_t x) {
 
 // ----------------------------------------------------------------- tune ----
 static void tune_defaults(bnx_tune *t) {
-    t->tile_log2 = 13;
+    t->tile_log2 = 14;
     t->seg_tiles = 8;
-    t->threads = 512;
+    t->threads = 256;
     t->ctas_per_sm = 0;
     t->small_q_log2 = 14;
     t->exact_tile = 0;
@@ -105,7 +105,8 @@ static int parse_tune_json(const char *s, bnx_tune *t) {
 // ---------------------------------------------------------- tables --------
 int build_pp_tables(bnx_ctx *c) {
     const uint32_t q_small = 1u << c->tune.small_q_log2;
-    const uint64_t lpp_cap = (uint64_t)c->np + 65536;
+    uint64_t lpp_cap = 2;
+    while (lpp_cap < (uint64_t)c->np + 65536) lpp_cap <<= 1;  // a power of two: the table is bitonic-sorted
     int rc;
     if ((rc = grow(c->spp, sizeof(SmallPP) * kMaxSpp))) return rc;
     if ((rc = grow(c->lpp, sizeof(LargePP) * lpp_cap))) return rc;
@@ -121,6 +122,13 @@ int build_pp_tables(bnx_ctx *c) {
     if (h[1] > lpp_cap) return fail(BNX_E_NOMEM, "large prime-power table overflow");
     c->n_spp = h[0];
     c->n_lpp = h[1];
+    {
+        uint32_t n2 = 2;
+        while (n2 < c->n_lpp) n2 <<= 1;
+        launch_sort_lpp((LargePP *)c->lpp.p, c->n_lpp, n2, c->stream);
+        CUDA_TRY(cudaGetLastError());
+        CUDA_TRY(cudaStreamSynchronize(c->stream));  // the copies below run on the default stream
+    }
     std::vector<SmallPP> hs(c->n_spp);
     if (c->n_spp) CUDA_TRY(cudaMemcpy(hs.data(), c->spp.p, sizeof(SmallPP) * c->n_spp, cudaMemcpyDeviceToHost));
     c->h_spp_q.resize(c->n_spp);
@@ -181,7 +189,7 @@ uint64_t bucket_bound(const bnx_ctx *c, uint64_t lo, uint64_t hi, uint64_t nseg)
 }
 
 int plan_host(bnx_ctx *c, const IvDev *iv, size_t k, PlanTotals *t) {
-    const uint32_t seg_log2 = c->seg_log2(), chunk_log2 = c->chunk_log2;
+    const uint32_t seg_log2 = c->seg_log2(), chunk_log2 = c->chunk_log2();
     t->segs = t->chunks = t->buckets = t->integers = 0;
     for (size_t i = 0; i < k; i++) {
         const uint64_t len = iv[i].hi - iv[i].lo;
@@ -242,7 +250,11 @@ Plan make_plan(const bnx_ctx *c) {
     P.n_lpp = c->n_lpp;
     P.tile_log2 = c->tune.tile_log2;
     P.seg_log2 = c->seg_log2();
-    P.chunk_log2 = c->chunk_log2;
+    P.chunk_log2 = c->chunk_log2();
+    {
+        const uint64_t qd = 1ull << (P.chunk_log2 - 8);
+        P.n_lpp_dense = (uint32_t)(std::upper_bound(c->lq.begin(), c->lq.end(), qd) - c->lq.begin());
+    }
     P.bcnt = (uint32_t *)c->bcnt.p;
     P.boff = (unsigned long long *)c->boff.p;
     P.bent = (uint2 *)c->bent.p;

@@ -97,17 +97,62 @@ __global__ void k_plan(IvDev *ivs, const uint32_t *n_iv_dev, uint32_t seg_log2, 
 }
 
 // ------------------------------------------------------------- buckets ----
-// Work unit: (chunk of sieved values of one interval, large prime power q).
-// Blocks stride over chunks; the threads of a block stride over the table.
-// Every multiple y of q in the chunk is a hit of its segment at offset y-seg_lo;
-// a multiple on a segment boundary is also the previous segment's halo value.
+// A bucket-fill chunk is 2^kChunkSegsLog2 whole queue segments of one interval
+// (the last chunk may be shorter).  One block owns a chunk: it finds every
+// multiple y of every large prime power q <= the chunk's last value and
+// records (y - seg_lo, p) for y's segment -- and, when y starts a segment, also
+// for the previous segment as its halo value.  Counts and write cursors of the
+// chunk's own segments live in shared memory; only a halo that belongs to the
+// previous chunk's last segment goes through a global counter (those entries
+// are written from the end of that segment's bucket, so the two writers never
+// meet).  Prime powers with many multiples per chunk (q <= 2^(chunk_log2-8))
+// are walked by a whole warp, the rest one thread each; the table is sorted by
+// q, so a thread stops at the first q above the chunk.
+constexpr uint32_t kChunkSegs = 1u << kChunkSegsLog2;
+
+__device__ __forceinline__ uint64_t fast_mod(uint64_t v, uint64_t q, uint64_t m) {
+    uint64_t r = v - q * __umul64hi(v, m);
+    return r >= q ? r - q : r;
+}
+
+template <bool FILL>
+__device__ __forceinline__ void bucket_hit(const Plan &P, const IvDev &iv, uint64_t y, uint32_t p, uint64_t nseg,
+                                           uint64_t s_first, uint32_t *hist, const unsigned long long *sbase) {
+    const uint64_t lseg = 1ull << P.seg_log2;
+    const uint64_t d = y - iv.lo;
+    const uint64_t s = d >> P.seg_log2;
+    const uint32_t o = (uint32_t)(d & (lseg - 1));
+    if (s < nseg) {
+        const uint32_t l = (uint32_t)(s - s_first);
+        const uint32_t pos = atomicAdd(&hist[l], 1u);
+        if (FILL) P.bent[sbase[l] + pos] = make_uint2(o, p);
+    }
+    if (o == 0 && s > 0) {
+        if (s > s_first) {  // halo of a segment of this chunk
+            const uint32_t l = (uint32_t)(s - 1 - s_first);
+            const uint32_t pos = atomicAdd(&hist[l], 1u);
+            if (FILL) P.bent[sbase[l] + pos] = make_uint2((uint32_t)lseg, p);
+        } else {  // halo of the previous chunk's last segment: written from its end
+            const uint64_t seg = iv.seg_base + s - 1;
+            const uint32_t pos = atomicAdd(&P.bcnt[seg], 1u);
+            if (FILL) P.bent[P.boff[seg + 1] - 1 - pos] = make_uint2((uint32_t)lseg, p);
+        }
+    }
+}
+
 template <bool FILL>
 __global__ void __launch_bounds__(256) k_bucket(Plan P) {
     __shared__ uint32_t s_iv;
+    __shared__ uint32_t hist[kChunkSegs];
+    __shared__ unsigned long long sbase[FILL ? kChunkSegs : 1];
     const uint64_t total_chunks = P.ctr->total_chunks;
     const uint32_t k = *P.n_iv;
-    const uint64_t lseg = 1ull << P.seg_log2;
+    const uint32_t lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
     if (FILL && blockIdx.x == 0 && threadIdx.x == 0) P.ctr->bucket_hits = P.boff[P.ctr->total_segs];
+    if (P.ctr->total_segs > P.seg_cap) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&P.ctr->err, kErrBucketOverflow);
+        return;
+    }
     for (uint64_t c = blockIdx.x; c < total_chunks; c += gridDim.x) {
         if (threadIdx.x == 0) s_iv = find_iv<false>(P.ivs, k, c);
         __syncthreads();
@@ -116,44 +161,34 @@ __global__ void __launch_bounds__(256) k_bucket(Plan P) {
         const uint64_t v0 = iv.lo + (c_in << P.chunk_log2);
         uint64_t v1 = v0 + (1ull << P.chunk_log2) - 1;
         if (v1 > iv.hi) v1 = iv.hi;
-        const uint64_t nseg = (iv.hi - iv.lo + lseg - 1) >> P.seg_log2;
-        for (uint32_t j = threadIdx.x; j < P.n_lpp; j += blockDim.x) {
-            const uint64_t q = P.lpp[j].q;
-            if (q > v1) continue;
-            const uint32_t p = P.lpp[j].p;
-            const uint64_t r = v0 % q;
-            for (uint64_t y = r ? v0 + (q - r) : v0; y <= v1; y += q) {
-                const uint64_t d = y - iv.lo;
-                const uint64_t s = d >> P.seg_log2;
-                const uint32_t o = (uint32_t)(d & (lseg - 1));
-#pragma unroll
-                for (int rep = 0; rep < 2; rep++) {
-                    uint64_t seg;
-                    uint32_t off;
-                    if (rep == 0) {
-                        if (s >= nseg) continue;
-                        seg = iv.seg_base + s;
-                        off = o;
-                    } else {
-                        if (o != 0 || s == 0) continue;
-                        seg = iv.seg_base + s - 1;  // halo of the previous segment
-                        off = (uint32_t)lseg;
-                    }
-                    if (seg >= P.seg_cap) {
-                        atomicOr(&P.ctr->err, kErrBucketOverflow);
-                        continue;
-                    }
-                    if (!FILL) {
-                        atomicAdd(&P.bcnt[seg], 1u);
-                    } else {
-                        const uint32_t pos = atomicAdd(&P.bcnt[seg], 1u);
-                        const unsigned long long at = P.boff[seg] + pos;
-                        if (at < P.boff[seg + 1] && at < P.bucket_cap) P.bent[at] = make_uint2(off, p);
-                        else atomicOr(&P.ctr->err, kErrBucketOverflow);
-                    }
-                }
-            }
+        const uint64_t nseg = (iv.hi - iv.lo + (1ull << P.seg_log2) - 1) >> P.seg_log2;
+        const uint64_t s_first = c_in << kChunkSegsLog2;
+        const uint32_t nsc = (uint32_t)(nseg - s_first < kChunkSegs ? nseg - s_first : kChunkSegs);
+        for (uint32_t i = threadIdx.x; i < kChunkSegs; i += blockDim.x) {
+            hist[i] = 0;
+            if (FILL && i < nsc) sbase[i] = P.boff[iv.seg_base + s_first + i];
         }
+        __syncthreads();
+        // dense prime powers: a warp per q, lanes on consecutive multiples
+        for (uint32_t j = warp; j < P.n_lpp_dense; j += nwarps) {
+            const LargePP e = P.lpp[j];
+            if (e.q > v1) break;
+            const uint64_t r = fast_mod(v0, e.q, e.m);
+            for (uint64_t y = (r ? v0 + (e.q - r) : v0) + lane * e.q; y <= v1; y += 32 * e.q)
+                bucket_hit<FILL>(P, iv, y, e.p, nseg, s_first, hist, sbase);
+        }
+        // sparse prime powers: a thread per q
+        for (uint32_t j = P.n_lpp_dense + threadIdx.x; j < P.n_lpp; j += blockDim.x) {
+            const LargePP e = P.lpp[j];
+            if (e.q > v1) break;
+            const uint64_t r = fast_mod(v0, e.q, e.m);
+            for (uint64_t y = r ? v0 + (e.q - r) : v0; y <= v1; y += e.q)
+                bucket_hit<FILL>(P, iv, y, e.p, nseg, s_first, hist, sbase);
+        }
+        __syncthreads();
+        if (!FILL)
+            for (uint32_t i = threadIdx.x; i < nsc; i += blockDim.x)
+                if (hist[i]) atomicAdd(&P.bcnt[iv.seg_base + s_first + i], hist[i]);
         __syncthreads();
     }
 }

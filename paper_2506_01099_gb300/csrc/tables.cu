@@ -106,6 +106,7 @@ __global__ void k_build_pp(const uint32_t *primes, uint32_t np, uint64_t max_hi,
             } else {
                 if (nl < lpp_cap) {
                     lpp[nl].q = q;
+                    lpp[nl].m = ~0ull / q;
                     lpp[nl].p = (uint32_t)p;
                     lpp[nl].pad = 0;
                 }
@@ -116,6 +117,30 @@ __global__ void k_build_pp(const uint32_t *primes, uint32_t np, uint64_t max_hi,
     }
     *n_spp = ns;
     *n_lpp = (uint32_t)nl;
+}
+
+// ---- bitonic sort of the large prime-power table by q (once per context) ----
+__global__ void k_pad_lpp(LargePP *lpp, uint32_t n_valid, uint32_t n_pow2) {
+    for (uint32_t i = n_valid + blockIdx.x * blockDim.x + threadIdx.x; i < n_pow2; i += gridDim.x * blockDim.x) {
+        lpp[i].q = ~0ull;
+        lpp[i].m = 1;
+        lpp[i].p = 0;
+        lpp[i].pad = 0;
+    }
+}
+
+__global__ void k_bitonic_step(LargePP *a, uint32_t n, uint32_t j, uint32_t k) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const uint32_t l = i ^ j;
+        if (l > i) {
+            const LargePP x = a[i], y = a[l];
+            const bool up = (i & k) == 0;
+            if ((x.q > y.q) == up) {
+                a[i] = y;
+                a[l] = x;
+            }
+        }
+    }
 }
 
 // ---- exclusive scan u32 -> u64 with the element count in device memory ----
@@ -246,5 +271,12 @@ void launch_exclusive_scan_u32(const uint32_t *in, unsigned long long *out, cons
 }
 
 uint32_t flags_blocks(uint64_t n) { return (uint32_t)((n + kFlagsPerBlock - 1) / kFlagsPerBlock); }
+
+void launch_sort_lpp(LargePP *lpp, uint32_t n_valid, uint32_t n_pow2, cudaStream_t s) {
+    const int grid = (int)((n_pow2 + 255) / 256 < 4096 ? (n_pow2 + 255) / 256 : 4096);
+    k_pad_lpp<<<grid, 256, 0, s>>>(lpp, n_valid, n_pow2);
+    for (uint32_t k = 2; k <= n_pow2; k <<= 1)
+        for (uint32_t j = k >> 1; j > 0; j >>= 1) k_bitonic_step<<<grid, 256, 0, s>>>(lpp, n_pow2, j, k);
+}
 
 }  // namespace bnx
