@@ -134,6 +134,29 @@ int bnx_prime_count(const bnx_ctx *ctx, uint64_t *out);
  * 1 <= len <= 2^31.  Errors: BNX_E_ARG, BNX_E_CUDA. */
 int bnx_rad_segment(bnx_ctx *ctx, uint64_t lo, uint64_t len, uint64_t *rad_out, uint64_t *sq_out, void *stream);
 
+/* Radicals of [lo, lo+len) without allocating any device memory -- for
+ * callers that cannot call cudaMalloc (their device memory is owned by another
+ * allocator or budget, or they run where allocation is not allowed).  The
+ * paper has no counterpart to this entry point; it returns what
+ * bnx_rad_segment returns, needs no context, and does all of its work in a
+ * fixed scratch array of BNX_NOALLOC_SCRATCH_BYTES compiled into the library,
+ * which every GPU that loads the library keeps until the process exits.
+ *  - rad_out / sq_out: caller DEVICE buffers of len uint64_t (sq_out may be
+ *    NULL); the work is queued on `stream` (NULL: the legacy default stream)
+ *    on the current device.
+ *  - Limits: 1 <= lo, 1 <= len <= BNX_NOALLOC_MAX_LEN, lo + len <= BNX_NOALLOC_MAX_HI;
+ *    anything larger is rejected with BNX_E_ARG.
+ *  - The first call on a device looks up the scratch's device address
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - Every call uses the same scratch: calls that may overlap on the GPU
+ *    (different streams, or threads without ordering) race.  Each call
+ *    re-initialises the scratch it reads, so back-to-back calls are independent.
+ * Errors: BNX_E_ARG, BNX_E_CUDA. */
+#define BNX_NOALLOC_MAX_LEN ((uint64_t)1 << 18)
+#define BNX_NOALLOC_MAX_HI ((uint64_t)1 << 40)
+#define BNX_NOALLOC_SCRATCH_BYTES 3145984u
+int bnx_rad_segment_noalloc(uint64_t lo, uint64_t len, uint64_t *rad_out, uint64_t *sq_out, void *stream);
+
 /* ------------------------------------------------------------------------ */
 /* Searches                                                                    */
 /* ------------------------------------------------------------------------ */

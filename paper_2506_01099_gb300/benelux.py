@@ -81,6 +81,7 @@ def lib(auto_build: bool = True):
             "bnx_get_stats": ([vp, P(bnx_stats)], i32),
             "bnx_prime_count": ([vp, P(u64)], i32),
             "bnx_rad_segment": ([vp, u64, u64, vp, vp, vp], i32),
+            "bnx_rad_segment_noalloc": ([u64, u64, vp, vp, vp], i32),
             "bnx_search": ([vp, u64, u64, u32, P(bnx_pair), sz, P(sz)], i32),
             "bnx_search_hash": ([vp, u64, u32, P(bnx_pair), sz, P(sz)], i32),
             "bnx_batch": ([vp, P(bnx_interval), sz, P(bnx_pair), sz, P(sz), P(u64)], i32),
@@ -156,6 +157,16 @@ def bnx_rad_segment(ctx, lo: int, length: int, rad_out_ptr: int, sq_out_ptr: int
                     stream: int | None = None) -> None:
     """Device pointers in, asynchronous on `stream`."""
     _check(lib().bnx_rad_segment(ctx, lo, length, rad_out_ptr, sq_out_ptr or None, stream or None))
+
+
+BNX_NOALLOC_MAX_LEN, BNX_NOALLOC_MAX_HI = 1 << 18, 1 << 40
+
+
+def bnx_rad_segment_noalloc(lo: int, length: int, rad_out_ptr: int, sq_out_ptr: int | None = None,
+                            stream: int | None = None) -> None:
+    """Like bnx_rad_segment, for callers that cannot allocate device memory: no
+    context, no allocation, fixed limits (length <= 2^18, lo + length <= 2^40)."""
+    _check(lib().bnx_rad_segment_noalloc(lo, length, rad_out_ptr, sq_out_ptr or None, stream or None))
 
 
 def _grow_call(fn, cap=256):
