@@ -1,0 +1,47 @@
+"""The multi-GPU path on CPU: two gloo ranks shard the batched workload with no
+data-path collective (weak scaling), and the timing reductions give the
+job-level numbers bench.py reports."""
+import os
+
+import pytest
+
+
+def _worker(rank, world, port, out):
+    import torch.distributed as dist
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    import bench
+    from paper_2506_01099_gb300 import workloads as W
+
+    ivs = bench.rank_intervals(rank, 64)
+    mine = W.total_integers(ivs)
+    total = bench.sum_over_ranks(world, float(mine))
+    slowest = bench.max_over_ranks(world, float(rank + 1))
+    out.put((rank, [(iv.lo, iv.hi, iv.kinds) for iv in ivs], mine, total, slowest))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_ranks_shard_without_exchange():
+    import multiprocessing as mp
+    import socket
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    procs = [ctx.Process(target=_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    res = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=60)
+        assert p.exitcode == 0
+    (r0, iv0, n0, t0, s0), (r1, iv1, n1, t1, s1) = res
+    assert (r0, r1) == (0, 1)
+    assert not set(iv0) & set(iv1)           # disjoint work, no shared interval
+    assert t0 == t1 == float(n0 + n1)        # value counts every rank's integers
+    assert s0 == s1 == 2.0                   # time = the slowest rank
+    assert all(2**32 <= lo < 2**40 and 2**16 <= hi - lo <= 2**30 for lo, hi, _ in iv0 + iv1)
