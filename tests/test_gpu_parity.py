@@ -228,3 +228,16 @@ def test_server_alone_vs_mix(B, ctx):
         pairs, lat = got[t]
         assert pairs == want
         assert lat > 0
+
+
+def test_theorem1_full_range(B):
+    """The paper's whole computation (Theorem 1): every pair of either kind with
+    n < 1.4e12 is one of the listed families or exceptional pairs."""
+    from paper_pins import THEOREM1_BOUND
+
+    with B.Context(0, max_hi=THEOREM1_BOUND) as c:
+        got = c.search(1, THEOREM1_BOUND)
+        st = c.stats()
+    assert got == theorem1_pairs(1, THEOREM1_BOUND)
+    assert len(got) == 41
+    assert st["integers"] == THEOREM1_BOUND - 1
