@@ -239,5 +239,5 @@ def test_theorem1_full_range(B):
         got = c.search(1, THEOREM1_BOUND)
         st = c.stats()
     assert got == theorem1_pairs(1, THEOREM1_BOUND)
-    assert len(got) == 41
+    assert len(got) == 42  # 20 of the first kind, 22 of the second
     assert st["integers"] == THEOREM1_BOUND - 1
