@@ -315,21 +315,24 @@ def run_ours(args):
         tp = time.perf_counter() - t0
         extras["plain_same_intervals"] = {"value": integers / tp, "unit": UNIT, "seconds": tp,
                                           "note": "one blocking bnx_search per interval, same 4096 intervals"}
-        # the large window at 2^40, plain (one call) vs batched (128 x 2^30)
-        lo, hi = W.LARGE_WINDOWS[0]
-        ctx.search(lo, lo + (1 << 30))
-        t0 = time.perf_counter()
-        p_plain = ctx.search(lo, hi)
-        tpw = time.perf_counter() - t0
-        wivs = W.large_window_intervals(0)
-        warr = B.make_intervals(wivs)
-        B.bnx_batch(ctx.h, wivs, warr)
-        t0 = time.perf_counter()
-        p_b, _ = B.bnx_batch(ctx.h, wivs, warr)
-        tbw = time.perf_counter() - t0
-        extras["window_2p40"] = {"range": [lo, hi], "plain": (hi - lo) / tpw, "batched": (hi - lo) / tbw,
-                                 "unit": UNIT, "pairs_plain": len(p_plain), "pairs_batched": len(p_b)}
+        # the large windows, plain (one call) vs batched (2^30-integer intervals)
+        for wi, name in ((0, "window_2p40"), (1, "window_1p3e12")):
+            lo, hi = W.LARGE_WINDOWS[wi]
+            ctx.search(lo, lo + (1 << 30))
+            t0 = time.perf_counter()
+            p_plain = ctx.search(lo, hi)
+            tpw = time.perf_counter() - t0
+            wivs = W.large_window_intervals(wi)
+            warr = B.make_intervals(wivs)
+            B.bnx_batch(ctx.h, wivs, warr)
+            t0 = time.perf_counter()
+            p_b, _ = B.bnx_batch(ctx.h, wivs, warr)
+            tbw = time.perf_counter() - t0
+            extras[name] = {"range": [lo, hi], "plain": (hi - lo) / tpw, "batched": (hi - lo) / tbw, "unit": UNIT,
+                            "pairs_plain": [list(p) for p in p_plain],
+                            "pairs_batched": [list(p[1:]) for p in p_b]}
         extras["serving"] = serve_stream(B, ctx, args, throughput=value / ws)
+        extras["serving_saturated"] = serve_stream(B, ctx, args, throughput=value / ws, saturate=True)
 
     if rank == 0:
         pk, pk_src = peaks()
@@ -379,12 +382,15 @@ def run_ours(args):
     return 0
 
 
-def serve_stream(B, ctx, args, throughput: float):
-    """Seeded Poisson stream at 0.7x the batched throughput; p50/p99 latency."""
+def serve_stream(B, ctx, args, throughput: float, saturate: bool = False):
+    """Seeded Poisson stream at 0.7x the batched throughput (or, saturated, every
+    request at t = 0); p50/p99 latency and integers/s."""
     n = args.serve_requests
     mean_len = W.mean_serving_length()
     rate = 0.7 * throughput / mean_len
     reqs = W.serving_requests(n, rate_per_s=rate)
+    if saturate:
+        reqs = [W.Request(0.0, r.interval) for r in reqs]
     B.bnx_server_start(ctx.h, max_active=args.serve_slots, slice_len=args.serve_slice)
     lat = {}
     tickets = {}
@@ -410,10 +416,12 @@ def serve_stream(B, ctx, args, throughput: float):
     span = time.perf_counter() - t0
     ls = sorted(lat.values())
     q = lambda p: ls[min(len(ls) - 1, int(math.ceil(p * len(ls))) - 1)] if ls else None
-    return {"requests": n, "completed": len(ls), "rate_per_s": rate, "p50_s": q(0.50), "p99_s": q(0.99),
+    return {"requests": n, "completed": len(ls), "rate_per_s": None if saturate else rate,
+            "p50_s": q(0.50), "p99_s": q(0.99),
             "integers_per_s": integers / span, "span_s": span, "slots": args.serve_slots, "slice": args.serve_slice,
-            "note": "seeded Poisson arrivals at 0.7x batched throughput / E[len]; len log-uniform [2^20, 2^34], "
-                    "lo uniform [1, 1.4e12], kinds 1|2|3"}
+            "note": ("all requests submitted at t = 0" if saturate else
+                     "seeded Poisson arrivals at 0.7x batched throughput / E[len]") +
+                    "; len log-uniform [2^20, 2^34], lo uniform [1, 1.4e12], kinds 1|2|3"}
 
 
 def profile_case():
@@ -441,7 +449,7 @@ def main():
     ap.add_argument("--autotune", action="store_true")
     ap.add_argument("--cpu-budget", type=float, default=2 ** 36)
     ap.add_argument("--ref-budget", type=float, default=2 ** 35)
-    ap.add_argument("--serve-requests", type=int, default=256)
+    ap.add_argument("--serve-requests", type=int, default=1024)
     ap.add_argument("--serve-slots", type=int, default=64)
     ap.add_argument("--serve-slice", type=int, default=1 << 28)
     ap.add_argument("--serve-timeout", type=float, default=120.0)
