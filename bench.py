@@ -357,8 +357,9 @@ def run_ours(args):
             "gpu_launches": KERNELS_PER_STEP * args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
                          "frac": achieved / alu_peak,
-                         "traffic": sieve_traffic(integers) if not ctx.tune()["exact_tile"] else None,
-                         "kernel": ("k_sieve_log<search>" if not ctx.tune()["exact_tile"] else "k_sieve<search>")
+                         "traffic": sieve_traffic(integers) if ctx.tune()["tile_kind"] == 0 else None,
+                         "kernel": {0: "k_sieve_log<search, u32 tile>", 1: "k_sieve<search, exact u64 tile>",
+                                    2: "k_sieve_log<search, u16 tile>"}[ctx.tune()["tile_kind"]]
                                    + " (persistent shared-memory tile sieve, fused filter + warp-ballot compaction)",
                          "peak_source": "152 SMs x 128 lanes/clk x max SM clock (issue roofline)",
                          "alg_ops_per_integer": ALG_OPS_PER_INT, "sieve_ms_per_launch": ms_sieve,

@@ -17,7 +17,10 @@
  *  - Return value: BNX_OK (0) or one of the BNX_E_* codes below; no C++
  *    exception crosses this boundary.  bnx_strerror() names a code, and
  *    bnx_last_error() gives the message of the last failure on this thread.
- *  - `kinds` is a bit mask: 1 = first kind, 2 = second kind, 3 = both.
+ *  - `kinds` is a bit mask: 1 = first kind, 2 = second kind, 4 = three-term
+ *    pairs (first-kind pairs with also rad(m+2) = rad(n+2): Erdos's original
+ *    question quoted in Sec. 1; reported with kind 4).  bnx_search_hash takes
+ *    1, 2 or 3.
  *  - Ranges: 1 <= lo < hi <= max_hi, where max_hi is fixed at bnx_create and is
  *    at most BNX_MAX_HI = 2^42 (so that 2n and every intermediate fit in 64 bits).
  *  - Output buffers are owned by the caller.  The library owns its device
@@ -53,7 +56,7 @@ extern "C" {
 
 typedef struct bnx_ctx bnx_ctx;
 
-/* One reported pair.  kind is 1 or 2. */
+/* One reported pair.  kind is 1, 2 or 4 (three-term). */
 typedef struct {
     uint64_t m, n;
     uint32_t kind;
@@ -75,8 +78,9 @@ typedef struct {
     uint32_t ctas_per_sm;  /* resident CTAs per SM for the persistent grid (0 = occupancy limit) */
     uint32_t small_q_log2; /* prime powers q <= 2^small_q_log2 are struck in shared
                               memory, larger ones come from the HBM buckets (8..16) */
-    uint32_t exact_tile;   /* searches: 0 = log-domain u32 tile with exact re-check of
-                              candidates (default), 1 = exact u64 square-part tile */
+    uint32_t tile_kind;    /* searches: 0 = log-domain u32 tile, 2 = log-domain u16 tile
+                              (both with exact re-check of candidates), 1 = exact u64
+                              square-part tile */
 } bnx_tune;
 
 /* Per-call counters of the last search on a context. */

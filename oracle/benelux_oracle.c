@@ -12,6 +12,8 @@
  *   rad(x)      product of the distinct primes dividing x, rad(1) = 1   (Sec. 2.1)
  *   first kind  1 <= m < n, rad(m) = rad(n) and rad(m+1) = rad(n+1)      (Sec. 1)
  *   second kind 1 <= m < n, rad(m) = rad(n+1) and rad(m+1) = rad(n)      (Sec. 1)
+ *   three-term  a first-kind pair with also rad(m+2) = rad(n+2): the question
+ *               Erdos asked, quoted in Sec. 1 (kind 4 in the output)
  *
  * The search contract is the one of Algorithm 3: for n in [lo, hi) report every
  * pair (m, n) of the requested kinds with any m < n.  Results are sorted by
@@ -218,9 +220,9 @@ static void push_pair(orc_pair *out, size_t cap, size_t *cnt, uint64_t m, uint64
  * of pairs (which may exceed cap; only cap are written).  N <= 2^14. */
 size_t orc_pairs_brute(uint64_t N, uint32_t kinds, orc_pair *out, size_t cap) {
     if (N < 2 || N > (1u << 14)) return 0;
-    uint64_t *r = (uint64_t *)malloc((N + 1) * sizeof(uint64_t));
+    uint64_t *r = (uint64_t *)malloc((N + 2) * sizeof(uint64_t));
     if (!r) return 0;
-    for (uint64_t x = 1; x <= N; x++) r[x] = orc_rad_td(x);
+    for (uint64_t x = 1; x <= N + 1; x++) r[x] = orc_rad_td(x);
     size_t cnt = 0;
     for (uint64_t n = 2; n < N; n++)
         for (uint64_t m = 1; m < n; m++) {
@@ -230,6 +232,8 @@ size_t orc_pairs_brute(uint64_t N, uint32_t kinds, orc_pair *out, size_t cap) {
             if ((kinds & 1) && r[m] == r[n] && r[m + 1] == r[n + 1]) push_pair(out, cap, &cnt, m, n, 1);
 #endif
             if ((kinds & 2) && r[m] == r[n + 1] && r[m + 1] == r[n]) push_pair(out, cap, &cnt, m, n, 2);
+            if ((kinds & 4) && r[m] == r[n] && r[m + 1] == r[n + 1] && r[m + 2] == r[n + 2])
+                push_pair(out, cap, &cnt, m, n, 4);
         }
     free(r);
     if (cnt && cnt <= cap) qsort(out, cnt, sizeof(orc_pair), cmp_pair);
@@ -336,12 +340,16 @@ static void crt_chunk(uint64_t c0, uint64_t c1, uint32_t kinds, uint64_t *r, pai
     for (uint64_t n = c0; n < c1; n++) {
         uint64_t a = r[n - c0], b2 = r[n + 1 - c0];
         u128 ab = (u128)a * b2;
-        if ((kinds & 1) && ab <= (u128)(n - 1)) {
+        if ((kinds & 5) && ab <= (u128)(n - 1)) {
             (*cnt1)++;
             uint64_t abl = (uint64_t)ab;
             for (uint64_t j = 1; j <= (n - 1) / abl; j++) {
                 uint64_t m = n - j * abl;
-                if (orc_rad_td(m) == a && orc_rad_td(m + 1) == b2) buf_push(b, m, n, 1);
+                if (orc_rad_td(m) == a && orc_rad_td(m + 1) == b2) {
+                    if (kinds & 1) buf_push(b, m, n, 1);
+                    /* three-term: also rad(m+2) = rad(n+2) (Erdos's question, Sec. 1) */
+                    if ((kinds & 4) && orc_rad_td(m + 2) == orc_rad_td(n + 2)) buf_push(b, m, n, 4);
+                }
             }
         }
 #if ORC_MUTANT == 6 /* mistake: the first-kind inequality applied to the second kind */
@@ -417,7 +425,8 @@ static size_t crt_run(uint64_t lo, uint64_t hi, uint32_t kinds, orc_pair *out, s
     return cnt;
 }
 
-/* Every pair (m, n) of the requested kinds (bit 1: first, bit 2: second) with
+/* Every pair (m, n) of the requested kinds (bit 1: first, bit 2: second, bit 4:
+ * three-term) with
  * lo <= n < hi and 1 <= m < n, sorted by (n, m, kind).  Returns the count (only
  * cap are written) or (size_t)-1 when memory ran out.  nthreads <= 0: all. */
 size_t orc_pairs_crt(uint64_t lo, uint64_t hi, uint32_t kinds, orc_pair *out, size_t cap, int nthreads) {

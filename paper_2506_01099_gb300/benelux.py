@@ -29,7 +29,7 @@ class bnx_interval(ctypes.Structure):
 
 class bnx_tune(ctypes.Structure):
     _fields_ = [("tile_log2", u32), ("seg_tiles", u32), ("threads", u32), ("ctas_per_sm", u32),
-                ("small_q_log2", u32), ("exact_tile", u32)]
+                ("small_q_log2", u32), ("tile_kind", u32)]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}

@@ -80,7 +80,7 @@ struct bnx_ctx {
     bool capturing = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_s0 = nullptr, ev_s1 = nullptr;
 
-    bnx::SieveCfg sieve_cfg[6];  // per (mode, tile kind)
+    bnx::SieveCfg sieve_cfg[9];  // per (mode, tile kind)
     bnx_stats stats{};
     std::mutex mu;
     bnx::Server *server = nullptr;

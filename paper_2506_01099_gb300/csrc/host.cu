@@ -60,17 +60,18 @@ static void tune_defaults(bnx_tune *t) {
     t->threads = 256;
     t->ctas_per_sm = 0;
     t->small_q_log2 = 14;
-    t->exact_tile = 0;
+    t->tile_kind = kTileLog32;
 }
 
 static int tune_check(const bnx_tune *t) {
-    if (t->tile_log2 < 10 || t->tile_log2 > 14) return fail(BNX_E_ARG, "tile_log2 must be in [10, 14]");
+    if (t->tile_log2 < 10 || t->tile_log2 > 15) return fail(BNX_E_ARG, "tile_log2 must be in [10, 15]");
+    if (t->tile_log2 == 15 && t->tile_kind != 2) return fail(BNX_E_ARG, "tile_log2 = 15 needs tile_kind 2");
     if (t->seg_tiles < 1 || t->seg_tiles > 64 || (t->seg_tiles & (t->seg_tiles - 1)))
         return fail(BNX_E_ARG, "seg_tiles must be a power of two in [1, 64]");
     if (t->threads != 128 && t->threads != 256 && t->threads != 512 && t->threads != 1024)
         return fail(BNX_E_ARG, "threads must be 128, 256, 512 or 1024");
     if (t->small_q_log2 < 8 || t->small_q_log2 > 16) return fail(BNX_E_ARG, "small_q_log2 must be in [8, 16]");
-    if (t->exact_tile > 1) return fail(BNX_E_ARG, "exact_tile must be 0 or 1");
+    if (t->tile_kind > 2) return fail(BNX_E_ARG, "tile_kind must be 0, 1 or 2");
     if (t->ctas_per_sm > 32) return fail(BNX_E_ARG, "ctas_per_sm must be <= 32");
     return BNX_OK;
 }
@@ -85,7 +86,7 @@ static int parse_tune_json(const char *s, bnx_tune *t) {
                   {"threads", &t->threads},
                   {"ctas_per_sm", &t->ctas_per_sm},
                   {"small_q_log2", &t->small_q_log2},
-                  {"exact_tile", &t->exact_tile}};
+                  {"tile_kind", &t->tile_kind}};
     for (const F &f : fields) {
         std::string key = std::string("\"") + f.name + "\"";
         const char *p = strstr(s, key.c_str());
@@ -285,12 +286,13 @@ Plan make_plan(const bnx_ctx *c) {
 
 // Launch shape of the persistent sieve for the current tuning (queried outside
 // any stream capture and cached until the tuning changes).
-static bool use_log_tile(const bnx_ctx *c, int mode) { return mode != kModeRad && c->tune.exact_tile == 0; }
+static bool use_log_tile(const bnx_ctx *c, int mode) { return mode != kModeRad && c->tune.tile_kind != kTileExact; }
+static bool use_w16(const bnx_ctx *c) { return c->tune.tile_kind == kTileLog16; }
 
 int sieve_config(bnx_ctx *c, int mode, int *grid, int *threads, size_t *smem) {
-    const bool lg = use_log_tile(c, mode);
-    SieveCfg &sc = c->sieve_cfg[mode * 2 + (lg ? 1 : 0)];
-    const size_t want_smem = lg ? sieve_log_smem_bytes(c->tune.tile_log2, c->n_spp, c->n_sched())
+    const bool lg = use_log_tile(c, mode), w16 = lg && use_w16(c);
+    SieveCfg &sc = c->sieve_cfg[mode * 3 + (lg ? (w16 ? 2 : 1) : 0)];
+    const size_t want_smem = lg ? sieve_log_smem_bytes(c->tune.tile_log2, c->n_spp, c->n_sched(), w16)
                                 : sieve_smem_bytes(c->tune.tile_log2, c->n_spp, c->n_sched());
     if (!sc.valid || sc.tile_log2 != c->tune.tile_log2 || sc.threads != c->tune.threads ||
         sc.ctas != c->tune.ctas_per_sm || sc.smem != want_smem) {
@@ -298,7 +300,7 @@ int sieve_config(bnx_ctx *c, int mode, int *grid, int *threads, size_t *smem) {
         const int thr = (int)c->tune.threads;
         const size_t smem_b = want_smem;
         int occ = 0;
-        int e = lg ? sieve_log_occupancy(mode, thr, smem_b, &occ) : sieve_occupancy(mode, thr, smem_b, &occ);
+        int e = lg ? sieve_log_occupancy(mode, thr, w16, smem_b, &occ) : sieve_occupancy(mode, thr, smem_b, &occ);
         if (e != 0) return fail(BNX_E_CUDA, "sieve occupancy query failed: %s", cudaGetErrorString((cudaError_t)e));
         if (occ < 1) return fail(BNX_E_ARG, "sieve kernel does not fit an SM with this tuning");
         const int per = c->tune.ctas_per_sm ? std::min<int>((int)c->tune.ctas_per_sm, occ) : occ;
@@ -333,7 +335,7 @@ int record_pipeline(bnx_ctx *c, int mode, cudaStream_t s, bool timing) {
     CUDA_TRY(cudaMemsetAsync(c->bcnt.p, 0, c->bcnt.bytes, s));
     launch_bucket(P, true, bgrid, s);
     if (timing) CUDA_TRY(cudaEventRecordWithFlags(c->ev_s0, s, c->capturing ? cudaEventRecordExternal : 0));
-    if (use_log_tile(c, mode)) launch_sieve_log(P, mode, sgrid, sthreads, ssmem, s);
+    if (use_log_tile(c, mode)) launch_sieve_log(P, mode, use_w16(c), sgrid, sthreads, ssmem, s);
     else launch_sieve(P, mode, sgrid, sthreads, ssmem, s);
     if (timing) CUDA_TRY(cudaEventRecordWithFlags(c->ev_s1, s, c->capturing ? cudaEventRecordExternal : 0));
     if (mode == kModeSearch) {
@@ -429,7 +431,7 @@ int validate_interval(const bnx_ctx *c, uint64_t lo, uint64_t hi, uint32_t kinds
                                         (unsigned long long)hi);
     if (hi > c->max_hi) return fail(BNX_E_ARG, "hi=%llu exceeds max_hi=%llu", (unsigned long long)hi,
                                     (unsigned long long)c->max_hi);
-    if (kinds < 1 || kinds > 3) return fail(BNX_E_ARG, "kinds must be 1, 2 or 3");
+    if (kinds < 1 || kinds > 7) return fail(BNX_E_ARG, "kinds must be a mask of 1, 2 and 4");
     return BNX_OK;
 }
 

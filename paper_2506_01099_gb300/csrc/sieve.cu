@@ -235,7 +235,7 @@ __device__ __noinline__ uint32_t exact_kinds(uint64_t n, uint64_t s0, uint64_t s
     const unsigned __int128 ab = (unsigned __int128)a * b;
     if (mode == kModeHash) return ab <= (unsigned __int128)2 * hash_S ? 3u : 0u;
     uint32_t r = 0;
-    if ((kinds & 1) && ab <= (unsigned __int128)(n - 1)) r |= 1;
+    if ((kinds & 5) && ab <= (unsigned __int128)(n - 1)) r |= 1;  // three-term pairs are first-kind pairs
     if ((kinds & 2) && ab <= (unsigned __int128)2 * n) {
         const uint64_t abl = (uint64_t)ab;
         const uint64_t jlo = (n + 2 + abl - 1) / abl, jhi = (2 * n) / abl;

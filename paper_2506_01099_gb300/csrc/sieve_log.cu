@@ -50,10 +50,13 @@ struct LogLayout {
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-__host__ __device__ inline LogLayout log_layout(uint32_t tile_log2, uint32_t nspp, uint32_t nsched) {
+// Tile words: one u32 per value, or (w16) two u16 values per u32 word; the
+// slack covers the epilogue's read past the last value.
+__host__ __device__ inline LogLayout log_layout(uint32_t tile_log2, uint32_t nspp, uint32_t nsched, bool w16) {
     LogLayout L;
     L.tile = 0;
-    L.spp = al16((((size_t)1 << tile_log2) + 8) * sizeof(uint32_t));
+    const size_t words = w16 ? ((size_t)1 << tile_log2) / 2 + 8 : ((size_t)1 << tile_log2) + 8;
+    L.spp = al16(words * sizeof(uint32_t));
     L.sched = L.spp + al16((size_t)4 * (nspp ? nspp : 1) * sizeof(uint32_t));
     L.bcache = L.sched + al16((size_t)(nsched ? nsched : 1) * sizeof(uint16_t));
     L.blg = L.bcache + (size_t)kLogBucketCache * sizeof(uint2);
@@ -66,6 +69,8 @@ __host__ __device__ inline LogLayout log_layout(uint32_t tile_log2, uint32_t nsp
 __device__ __forceinline__ uint32_t lg_large(uint32_t p) {
     return __float2uint_rd(log2f((float)p) * 65536.0f) + 4u;
 }
+// the same in units of 2^-8 (u16 tile); 2 units cover the error and the truncation
+__device__ __forceinline__ uint32_t lg_large8(uint32_t p) { return __float2uint_rd(log2f((float)p) * 256.0f) + 2u; }
 
 struct SmallPrimes {
     uint32_t n;
@@ -111,7 +116,7 @@ __device__ __noinline__ uint32_t exact_kinds_log(uint64_t n, uint64_t s0, uint64
     const unsigned __int128 ab = (unsigned __int128)a * b;
     if (mode == kModeHash) return ab <= (unsigned __int128)2 * hash_S ? 3u : 0u;
     uint32_t r = 0;
-    if ((kinds & 1) && ab <= (unsigned __int128)(n - 1)) r |= 1;
+    if ((kinds & 5) && ab <= (unsigned __int128)(n - 1)) r |= 1;  // three-term pairs are first-kind pairs
     if ((kinds & 2) && ab <= (unsigned __int128)2 * n) {
         const uint64_t abl = (uint64_t)ab;
         const uint64_t jlo = (n + 2 + abl - 1) / abl, jhi = (2 * n) / abl;
@@ -125,13 +130,17 @@ struct LogMinBlocks {  // 64 registers per thread at every CTA size
     static constexpr int value = NT <= 128 ? 8 : NT <= 256 ? 4 : NT <= 512 ? 2 : 1;
 };
 
-template <int MODE, int NT>
+// W16: the tile keeps L(x) in 16 bits with 8 fractional bits (two values per
+// 32-bit word; a sum stays below 42*2^8 + 42 < 2^15, so a strike's addition of
+// lg << 16*(x&1) never carries into the neighbour, and a pair sum stays below 2^16).
+template <int MODE, int NT, bool W16>
 __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
+    constexpr uint32_t FS = W16 ? 256u : 65536u;  // fixed-point scale of L
     const uint32_t tile_log2 = P.tile_log2;
     const uint32_t LT = 1u << tile_log2;
     const uint32_t nspp = P.n_spp;
-    const LogLayout lay = log_layout(tile_log2, nspp, P.n_sched);
+    const LogLayout lay = log_layout(tile_log2, nspp, P.n_sched, W16);
     uint32_t *tile = reinterpret_cast<uint32_t *>(smem_raw + lay.tile);
     uint32_t *sq = reinterpret_cast<uint32_t *>(smem_raw + lay.spp);
     uint32_t *slg = sq + nspp;
@@ -153,7 +162,7 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
     for (uint32_t j = tid; j < nspp; j += NT) {
         const SmallPP e = P.spp[j];
         sq[j] = e.q;
-        slg[j] = e.lg;
+        slg[j] = W16 ? (uint32_t)floor(log2((double)e.p) * 256.0) + 1u : e.lg;
         slmod[j] = LT % e.q;
     }
     if (tid == 0) {
@@ -221,7 +230,7 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
         for (uint32_t e = tid; e < nbc; e += NT) {
             const uint2 h = P.bent[b0 + e];
             bcache[e] = h;
-            blg[e] = lg_large(h.y);
+            blg[e] = W16 ? lg_large8(h.y) : lg_large(h.y);
         }
         const uint32_t nsched = s_nsched;
         const uint32_t kinds = iv.kinds;
@@ -239,57 +248,86 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
                 const int clog = (int)flog2_64(S2) + ((S2 & (S2 - 1)) ? 1 : 0);
                 lthr = (int)flog2_64(t_lo) + (int)flog2_64(t_lo + 1) - clog;  // need log2 P >= log2(n(n+1)/2S)
             }
-            T = ((int64_t)lthr - (int64_t)(kHigh2 - 2)) * 65536;
+            T = ((int64_t)lthr - (int64_t)(kHigh2 - 2)) * FS;
             const bool all_cand = T <= 0;
             const uint32_t T32 = all_cand ? 0u : (uint32_t)T;
             __syncthreads();
             {
                 uint4 *t4 = reinterpret_cast<uint4 *>(tile);
                 const uint4 z = make_uint4(0, 0, 0, 0);
-                for (uint32_t i = tid; i <= ((tl + 4) >> 2); i += NT) t4[i] = z;
+                const uint32_t n4 = W16 ? ((tl >> 1) + 8 + 3) >> 2 : ((tl + 4) >> 2) + 1;
+                for (uint32_t i = tid; i < n4; i += NT) t4[i] = z;
             }
             __syncthreads();
             for (uint32_t g = warp; g < nsched; g += nwarps) {
                 const uint32_t e = sched[g];
                 const uint32_t j = e & 255u;
                 const uint32_t x = soff[j] + (((e >> 8) << 5) + lane) * sq[j];
-                if (x <= tl) atomicAdd(&tile[x], slg[j]);
+                if (x <= tl) {
+                    if (W16) atomicAdd(&tile[x >> 1], slg[j] << ((x & 1) << 4));
+                    else atomicAdd(&tile[x], slg[j]);
+                }
             }
             for (uint32_t e = tid; e < nbc; e += NT) {
                 const uint2 h = bcache[e];
-                if (h.x >= t0 && h.x <= t0 + tl) atomicAdd(&tile[h.x - t0], blg[e]);
+                if (h.x >= t0 && h.x <= t0 + tl) {
+                    const uint32_t x = h.x - t0;
+                    if (W16) atomicAdd(&tile[x >> 1], blg[e] << ((x & 1) << 4));
+                    else atomicAdd(&tile[x], blg[e]);
+                }
             }
             for (unsigned long long e = b0 + kLogBucketCache + tid; e < b1; e += NT) {
                 const uint2 h = P.bent[e];
-                if (h.x >= t0 && h.x <= t0 + tl) atomicAdd(&tile[h.x - t0], lg_large(h.y));
+                if (h.x >= t0 && h.x <= t0 + tl) {
+                    const uint32_t x = h.x - t0;
+                    if (W16) atomicAdd(&tile[x >> 1], lg_large8(h.y) << ((x & 1) << 4));
+                    else atomicAdd(&tile[x], lg_large(h.y));
+                }
             }
             __syncthreads();
             for (uint32_t j = tid; j < nspp; j += NT) {
                 const uint32_t off = soff[j], lm = slmod[j];
                 soff[j] = off >= lm ? off - lm : off + sq[j] - lm;
             }
-            // epilogue: four consecutive n per thread
+            // epilogue: G consecutive n per thread (4 u32 values, or 8 u16 values, per 16-byte load)
             constexpr uint32_t M2 = 1u << kHigh2;
-            const uint32_t ngroups = (tl + 3) >> 2;
+            constexpr uint32_t G = W16 ? 8u : 4u;
+            const uint32_t ngroups = (tl + G - 1) / G;
             const uint4 *t4 = reinterpret_cast<const uint4 *>(tile);
             for (uint32_t base = 0; base < ngroups; base += NT) {
                 const uint32_t g = base + tid;
-                uint32_t cm = 0;  // candidates among the group's four n (bit u: n = t_lo + 4g + u)
+                uint32_t cm = 0;  // candidates among the group's n (bit u: n = t_lo + G*g + u)
                 if (g < ngroups) {
                     const uint4 v = t4[g];
                     const uint32_t w = tile[4 * g + 4];
-                    const uint32_t s0 = v.x + v.y, s1 = v.y + v.z, s2 = v.z + v.w, s3 = v.w + w;
-                    const uint32_t mx = max(max(s0, s1), max(s2, s3));
-                    const uint32_t n0 = (uint32_t)(t_lo + 4 * g);  // low 32 bits suffice modulo 2^M
-                    // does [n0, n0 + 4] hold a multiple of 2^M?
-                    const bool hi2 = ((n0 + 4u) & (M2 - 1)) <= 4u;
+                    uint32_t mx;
+                    uint32_t ss[G];
+                    if constexpr (W16) {
+                        // packed pair sums: low half L(2k) + L(2k+1), high half L(2k+1) + L(2k+2)
+                        const uint32_t p0 = v.x + __funnelshift_r(v.x, v.y, 16);
+                        const uint32_t p1 = v.y + __funnelshift_r(v.y, v.z, 16);
+                        const uint32_t p2 = v.z + __funnelshift_r(v.z, v.w, 16);
+                        const uint32_t p3 = v.w + __funnelshift_r(v.w, w, 16);
+                        const uint32_t m2 = __vmaxu2(__vmaxu2(p0, p1), __vmaxu2(p2, p3));
+                        mx = max(m2 & 0xffffu, m2 >> 16);
+                        ss[0] = p0 & 0xffffu; ss[1] = p0 >> 16; ss[2] = p1 & 0xffffu; ss[3] = p1 >> 16;
+                        ss[4] = p2 & 0xffffu; ss[5] = p2 >> 16; ss[6] = p3 & 0xffffu; ss[7] = p3 >> 16;
+                    } else {
+                        ss[0] = v.x + v.y;
+                        ss[1] = v.y + v.z;
+                        ss[2] = v.z + v.w;
+                        ss[3] = v.w + w;
+                        mx = max(max(ss[0], ss[1]), max(ss[2], ss[3]));
+                    }
+                    const uint32_t n0 = (uint32_t)(t_lo + G * g);  // low 32 bits suffice modulo 2^M
+                    // does [n0, n0 + G] hold a multiple of 2^M?
+                    const bool hi2 = ((n0 + G) & (M2 - 1)) <= G;
                     if (all_cand || mx >= T32 || hi2) {
-                        const uint32_t ss[4] = {s0, s1, s2, s3};
 #pragma unroll
-                        for (uint32_t u = 0; u < 4; u++) {
+                        for (uint32_t u = 0; u < G; u++) {
                             const uint32_t nl = n0 + u;
                             const bool h = ((nl & (M2 - 1)) == 0) || (((nl + 1) & (M2 - 1)) == 0);
-                            if ((all_cand || ss[u] >= T32 || h) && 4 * g + u < tl) cm |= 1u << u;
+                            if ((all_cand || ss[u] >= T32 || h) && G * g + u < tl) cm |= 1u << u;
                         }
                     }
                 }
@@ -299,11 +337,13 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
                     if (cm) {
                         const uint32_t u = (uint32_t)(__ffs(cm) - 1);
                         cm &= cm - 1;
-                        const uint32_t i = 4 * g + u;
+                        const uint32_t i = G * g + u;
                         n = t_lo + i;
                         const uint32_t e2 = ctz64(n + (n & 1)) - 1;  // power of 2 in P
-                        const int64_t ub = (int64_t)(tile[i] + tile[i + 1]) + (int64_t)e2 * 65536;
-                        int need;  // log2 P <= ub / 2^16 must reach it
+                        const uint32_t L0 = W16 ? (tile[i >> 1] >> ((i & 1) << 4)) & 0xffffu : tile[i];
+                        const uint32_t L1 = W16 ? (tile[(i + 1) >> 1] >> (((i + 1) & 1) << 4)) & 0xffffu : tile[i + 1];
+                        const int64_t ub = (int64_t)(L0 + L1) + (int64_t)e2 * FS;
+                        int need;  // log2 P <= ub / FS must reach it
                         if (MODE == kModeSearch) {
                             need = (int)flog2_64(n + 1) - 1;
                         } else {
@@ -311,7 +351,7 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
                             need = (int)flog2_64(n) + (int)flog2_64(n + 1) - (int)flog2_64(S2) -
                                    ((S2 & (S2 - 1)) ? 1 : 0);
                         }
-                        if (ub >= (int64_t)need * 65536) {
+                        if (ub >= (int64_t)need * FS) {
                             const uint64_t s0 = sodd_exact(n, t0 + i, &sprimes, P.sqrt_q, bcache, nbc, P.bent,
                                                            b0 + kLogBucketCache, b1);
                             const uint64_t s1 = sodd_exact(n + 1, t0 + i + 1, &sprimes, P.sqrt_q, bcache, nbc,
@@ -349,36 +389,37 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
     }
 }
 
-template <int MODE>
+template <int MODE, bool W16>
 const void *log_fn_t(int threads) {
     switch (threads) {
-        case 128: return (const void *)k_sieve_log<MODE, 128>;
-        case 256: return (const void *)k_sieve_log<MODE, 256>;
-        case 512: return (const void *)k_sieve_log<MODE, 512>;
-        default: return (const void *)k_sieve_log<MODE, 1024>;
+        case 128: return (const void *)k_sieve_log<MODE, 128, W16>;
+        case 256: return (const void *)k_sieve_log<MODE, 256, W16>;
+        case 512: return (const void *)k_sieve_log<MODE, 512, W16>;
+        default: return (const void *)k_sieve_log<MODE, 1024, W16>;
     }
 }
 
-const void *log_fn(int mode, int threads) {
-    return mode == kModeHash ? log_fn_t<kModeHash>(threads) : log_fn_t<kModeSearch>(threads);
+const void *log_fn(int mode, int threads, bool w16) {
+    if (w16) return mode == kModeHash ? log_fn_t<kModeHash, true>(threads) : log_fn_t<kModeSearch, true>(threads);
+    return mode == kModeHash ? log_fn_t<kModeHash, false>(threads) : log_fn_t<kModeSearch, false>(threads);
 }
 
 }  // namespace
 
-size_t sieve_log_smem_bytes(uint32_t tile_log2, uint32_t nspp, uint32_t nsched) {
-    return log_layout(tile_log2, nspp, nsched).total;
+size_t sieve_log_smem_bytes(uint32_t tile_log2, uint32_t nspp, uint32_t nsched, bool w16) {
+    return log_layout(tile_log2, nspp, nsched, w16).total;
 }
 
-int sieve_log_occupancy(int mode, int threads, size_t smem, int *ctas_per_sm) {
-    const void *fn = log_fn(mode, threads);
+int sieve_log_occupancy(int mode, int threads, bool w16, size_t smem, int *ctas_per_sm) {
+    const void *fn = log_fn(mode, threads, w16);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, fn, threads, smem);
 }
 
-void launch_sieve_log(const Plan &P, int mode, int grid, int threads, size_t smem, cudaStream_t s) {
+void launch_sieve_log(const Plan &P, int mode, bool w16, int grid, int threads, size_t smem, cudaStream_t s) {
     void *args[] = {(void *)&P};
-    cudaLaunchKernel(log_fn(mode, threads), dim3(grid), dim3(threads), args, smem, s);
+    cudaLaunchKernel(log_fn(mode, threads, w16), dim3(grid), dim3(threads), args, smem, s);
 }
 
 }  // namespace bnx

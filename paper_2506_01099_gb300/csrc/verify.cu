@@ -51,6 +51,18 @@ __device__ __forceinline__ bool rad_is(uint64_t m, uint64_t r) {
     return true;
 }
 
+// rad(x) == rad(y): every prime of x divides y and every prime of y divides x
+__device__ __forceinline__ bool strip_by(uint64_t x, uint64_t y) {
+    while (x > 1) {
+        const uint64_t g = gcd64(x, y);
+        if (g == 1) return false;
+        x /= g;
+    }
+    return true;
+}
+
+__device__ __forceinline__ bool same_rad(uint64_t x, uint64_t y) { return strip_by(x, y) && strip_by(y, x); }
+
 __device__ __forceinline__ void emit_pair(const Plan &P, uint64_t m, uint64_t n, uint32_t kind, uint32_t iv) {
     const unsigned long long at = atomicAdd(&P.ctr->n_pairs, 1ull);
     if (at < P.pair_cap) {
@@ -76,12 +88,17 @@ __global__ void k_verify(Plan P) {
         const uint64_t n = s.n;
         const uint64_t ab = s.a * s.b;  // <= 2n: passed the filter
         unsigned long long cands = 0;
+        const uint32_t want = P.ivs[s.iv].kinds;
         if (s.kinds & 1) {
             const uint64_t J = (n - 1) / ab;
             cands += J;
             for (uint64_t j = 1 + lane; j <= J; j += 32) {
                 const uint64_t m = n - j * ab;
-                if (rad_is(m, s.a) && rad_is(m + 1, s.b)) emit_pair(P, m, n, 1, s.iv);
+                if (rad_is(m, s.a) && rad_is(m + 1, s.b)) {
+                    if (want & 1) emit_pair(P, m, n, 1, s.iv);
+                    // Erdos's three-term question (Sec. 1): also rad(m+2) = rad(n+2)
+                    if ((want & 4) && same_rad(m + 2, n + 2)) emit_pair(P, m, n, 4, s.iv);
+                }
             }
         }
         if (s.kinds & 2) {

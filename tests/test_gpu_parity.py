@@ -80,8 +80,11 @@ def test_rad_segment_large_sampled(ctx, orc):
 @pytest.mark.parametrize("tune", [dict(tile_log2=12, seg_tiles=1, small_q_log2=10),
                                   dict(tile_log2=14, seg_tiles=4, threads=1024, small_q_log2=16),
                                   dict(tile_log2=11, seg_tiles=16, threads=256, small_q_log2=8),
-                                  dict(exact_tile=1),
-                                  dict(exact_tile=1, tile_log2=12, threads=256, small_q_log2=12)])
+                                  dict(tile_kind=1),
+                                  dict(tile_kind=1, tile_log2=12, threads=256, small_q_log2=12),
+                                  dict(tile_kind=2),
+                                  dict(tile_kind=2, tile_log2=13, threads=128, small_q_log2=16),
+                                  dict(tile_kind=2, tile_log2=14, threads=512, seg_tiles=2, small_q_log2=10)])
 def test_tunings_agree(B, orc, tune):
     with B.Context(0, max_hi=1 << 41) as c:
         c.set_tune(**tune)
@@ -196,7 +199,7 @@ def test_batch_family_members(ctx):
 
 
 def test_bad_arguments(B, ctx):
-    for args in ((0, 10, 3), (10, 10, 3), (5, 4, 3), (1, MAX_HI + 1, 3), (1, 10, 0), (1, 10, 4)):
+    for args in ((0, 10, 3), (10, 10, 3), (5, 4, 3), (1, MAX_HI + 1, 3), (1, 10, 0), (1, 10, 8)):
         with pytest.raises(B.BnxError) as e:
             ctx.search(*args)
         assert e.value.code == B.BNX_E_ARG
@@ -236,8 +239,16 @@ def test_theorem1_full_range(B):
     from paper_pins import THEOREM1_BOUND
 
     with B.Context(0, max_hi=THEOREM1_BOUND) as c:
-        got = c.search(1, THEOREM1_BOUND)
+        got = c.search(1, THEOREM1_BOUND, 7)  # both kinds and the three-term question
         st = c.stats()
-    assert got == theorem1_pairs(1, THEOREM1_BOUND)
+    assert got == theorem1_pairs(1, THEOREM1_BOUND)  # in particular, no three-term pair
     assert len(got) == 42  # 20 of the first kind, 22 of the second
     assert st["integers"] == THEOREM1_BOUND - 1
+
+
+def test_three_term_kind(ctx, orc):
+    """Bit 4 (Erdos's three-term question) reports nothing where the oracle does not."""
+    assert ctx.search(1, 1 << 22, 4) == orc.pairs_crt(1, 1 << 22, 4) == []
+    assert ctx.search(1, 1 << 32, 5) == theorem1_pairs(1, 1 << 32, 1)
+    lo = 2**40 - 2**22
+    assert ctx.search(lo, lo + 2**23, 6) == orc.pairs_crt(lo, lo + 2**23, 6)

@@ -196,3 +196,17 @@ def test_planted_mistake_is_caught(k, tmp_path):
         if failures:
             break
     assert failures, f"no pin caught mutant {k}: {MUTANTS[k]}"
+
+
+def test_three_term_question(orc):
+    """Erdos's original question (Sec. 1): rad(m+i) = rad(n+i) for i = 0, 1, 2.
+    Sec. 1 shows why the families fail it (m+2 = 2^(k+1) while n+2 = 2 mod 4)
+    and that (75, 1215) fails it (77 = 7*11, 1217 prime); no solution is known."""
+    for m, n, kind in theorem1_pairs(1, 1 << 40, 1):
+        assert orc.rad_td(m + 2) != orc.rad_td(n + 2), (m, n)
+    assert orc.rad_td(77) == 77 and orc.rad_td(1217) == 1217
+    assert orc.pairs_brute(1 << 12, 4) == []
+    assert orc.pairs_crt(1, 1 << 22, 4) == []
+    # bit 4 adds nothing to bit 1, and the brute force agrees with the CRT path
+    assert orc.pairs_crt(1, 1 << 22, 5) == theorem1_pairs(1, 1 << 22, 1)
+    assert orc.pairs_brute(1 << 12, 7) == theorem1_pairs(1, 1 << 12, 3)
