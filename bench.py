@@ -111,7 +111,7 @@ def sieve_traffic(integers: int):
     import hashlib
 
     try:
-        rec = json.load(open(os.path.join(ROOT, "profiles", "k_sieve_log_traffic.json")))
+        rec = json.load(open(os.path.join(ROOT, "profiles", "k_sieve_log_u16_traffic.json")))
         src = open(os.path.join(ROOT, rec["source"]), "rb").read()
     except Exception:
         return None
@@ -247,7 +247,7 @@ def run_ours(args):
     from paper_2506_01099_gb300 import benelux as B
 
     gpu_name = torch.cuda.get_device_name(local)
-    tune_json = load_tune(gpu_name)
+    tune_json = merged_tune(gpu_name, args.tune)
     stream = torch.cuda.current_stream()
     ctx = B.Context(local, max_hi=MAX_HI, tune_json=tune_json, stream=stream.cuda_stream)
     if args.autotune:
@@ -357,7 +357,7 @@ def run_ours(args):
             "gpu_launches": KERNELS_PER_STEP * args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
                          "frac": achieved / alu_peak,
-                         "traffic": sieve_traffic(integers) if ctx.tune()["tile_kind"] == 0 else None,
+                         "traffic": sieve_traffic(integers) if ctx.tune()["tile_kind"] == 2 else None,
                          "kernel": {0: "k_sieve_log<search, u32 tile>", 1: "k_sieve<search, exact u64 tile>",
                                     2: "k_sieve_log<search, u16 tile>"}[ctx.tune()["tile_kind"]]
                                    + " (persistent shared-memory tile sieve, fused filter + warp-ballot compaction)",
@@ -425,12 +425,20 @@ def serve_stream(B, ctx, args, throughput: float, saturate: bool = False):
                     "; len log-uniform [2^20, 2^34], lo uniform [1, 1.4e12], kinds 1|2|3"}
 
 
-def profile_case():
+def merged_tune(gpu_name: str, override: str | None) -> str | None:
+    """The cached tuning for this GPU with the fields of `override` (JSON) on top."""
+    base = json.loads(load_tune(gpu_name) or "{}")
+    if override:
+        base.update(json.loads(override))
+    return json.dumps(base) if base else None
+
+
+def profile_case(override: str | None = None):
     import torch
 
     from paper_2506_01099_gb300 import benelux as B
 
-    ctx = B.Context(0, max_hi=MAX_HI, tune_json=load_tune(torch.cuda.get_device_name(0)))
+    ctx = B.Context(0, max_hi=MAX_HI, tune_json=merged_tune(torch.cuda.get_device_name(0), override))
     lo = 1 << 40
     ctx.search(lo, lo + (1 << 20))
     pairs = ctx.search(lo, lo + (1 << 28))
@@ -454,11 +462,12 @@ def main():
     ap.add_argument("--serve-slots", type=int, default=64)
     ap.add_argument("--serve-slice", type=int, default=1 << 28)
     ap.add_argument("--serve-timeout", type=float, default=120.0)
+    ap.add_argument("--tune", default=None, help="JSON of bnx_tune fields applied over the cached tuning")
     ap.add_argument("--profile-case", action="store_true",
                     help="one warm-up and one search of [2^40, 2^40 + 2^28) (small case for ncu), then exit")
     args = ap.parse_args()
     if args.profile_case:
-        return profile_case()
+        return profile_case(args.tune)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

@@ -60,7 +60,7 @@ static void tune_defaults(bnx_tune *t) {
     t->threads = 256;
     t->ctas_per_sm = 0;
     t->small_q_log2 = 14;
-    t->tile_kind = kTileLog32;
+    t->tile_kind = kTileLog16;
 }
 
 static int tune_check(const bnx_tune *t) {

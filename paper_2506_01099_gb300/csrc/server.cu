@@ -258,8 +258,9 @@ int bnx_autotune(bnx_ctx *c, const bnx_interval *iv, size_t k, int rounds, char 
     const uint32_t thr[] = {128, 256, 512, 1024};
     const uint32_t qs[] = {12, 13, 14, 15, 16};
     const uint32_t ctas[] = {0, 1, 2};
+    const uint32_t kinds[] = {0, 2};
     for (int pass = 0; pass < 2; pass++) {
-        for (int field = 0; field < 5; field++) {
+        for (int field = 0; field < 6; field++) {
             const uint32_t *vals;
             int nv;
             switch (field) {
@@ -267,12 +268,17 @@ int bnx_autotune(bnx_ctx *c, const bnx_interval *iv, size_t k, int rounds, char 
                 case 1: vals = segt; nv = 5; break;
                 case 2: vals = thr; nv = 4; break;
                 case 3: vals = qs; nv = 5; break;
-                default: vals = ctas; nv = 3; break;
+                case 4: vals = ctas; nv = 3; break;
+                default: vals = kinds; nv = 2; break;
             }
             for (int v = 0; v < nv; v++) {
                 bnx_tune t = best;
-                uint32_t *f = field == 0 ? &t.tile_log2 : field == 1 ? &t.seg_tiles : field == 2 ? &t.threads
-                                                      : field == 3 ? &t.small_q_log2 : &t.ctas_per_sm;
+                uint32_t *f = field == 0   ? &t.tile_log2
+                              : field == 1 ? &t.seg_tiles
+                              : field == 2 ? &t.threads
+                              : field == 3 ? &t.small_q_log2
+                              : field == 4 ? &t.ctas_per_sm
+                                           : &t.tile_kind;
                 if (*f == vals[v]) continue;
                 *f = vals[v];
                 float ms = 0;
@@ -289,8 +295,9 @@ int bnx_autotune(bnx_ctx *c, const bnx_interval *iv, size_t k, int rounds, char 
     if (json_out && json_cap) {
         snprintf(json_out, json_cap,
                  "{\"tile_log2\": %u, \"seg_tiles\": %u, \"threads\": %u, \"ctas_per_sm\": %u, "
-                 "\"small_q_log2\": %u, \"ms\": %.4f}",
-                 best.tile_log2, best.seg_tiles, best.threads, best.ctas_per_sm, best.small_q_log2, best_ms);
+                 "\"small_q_log2\": %u, \"tile_kind\": %u, \"ms\": %.4f}",
+                 best.tile_log2, best.seg_tiles, best.threads, best.ctas_per_sm, best.small_q_log2, best.tile_kind,
+                 best_ms);
     }
     return BNX_OK;
 }
