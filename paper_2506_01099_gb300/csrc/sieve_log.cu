@@ -28,6 +28,7 @@ namespace {
 constexpr int kLogBucketCache = 256;
 constexpr uint32_t kHigh2 = 16;
 constexpr int kMaxSmallPrimes = 64;
+constexpr uint32_t kRoundsPerEntry = 4;  // a schedule entry strikes up to 4 x 32 multiples of one q
 
 __device__ __forceinline__ uint32_t ctz64(uint64_t x) { return (uint32_t)(__ffsll((long long)x) - 1); }
 __device__ __forceinline__ uint32_t flog2_64(uint64_t x) { return 63u - (uint32_t)__clzll((long long)x); }
@@ -57,7 +58,7 @@ __host__ __device__ inline LogLayout log_layout(uint32_t tile_log2, uint32_t nsp
     L.tile = 0;
     const size_t words = w16 ? ((size_t)1 << tile_log2) / 2 + 8 : ((size_t)1 << tile_log2) + 8;
     L.spp = al16(words * sizeof(uint32_t));
-    L.sched = L.spp + al16((size_t)4 * (nspp ? nspp : 1) * sizeof(uint32_t));
+    L.sched = L.spp + al16((size_t)5 * (nspp ? nspp : 1) * sizeof(uint32_t));
     L.bcache = L.sched + al16((size_t)(nsched ? nsched : 1) * sizeof(uint16_t));
     L.blg = L.bcache + (size_t)kLogBucketCache * sizeof(uint2);
     L.total = L.blg + (size_t)kLogBucketCache * sizeof(uint32_t);
@@ -146,6 +147,7 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
     uint32_t *slg = sq + nspp;
     uint32_t *soff = slg + nspp;
     uint32_t *slmod = soff + nspp;
+    uint32_t *srounds = slmod + nspp;  // 32-multiple rounds of q in a tile
     uint16_t *sched = reinterpret_cast<uint16_t *>(smem_raw + lay.sched);
     uint2 *bcache = reinterpret_cast<uint2 *>(smem_raw + lay.bcache);
     uint32_t *blg = reinterpret_cast<uint32_t *>(smem_raw + lay.blg);
@@ -164,6 +166,7 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
         sq[j] = e.q;
         slg[j] = W16 ? (uint32_t)floor(log2((double)e.p) * 256.0) + 1u : e.lg;
         slmod[j] = LT % e.q;
+        srounds[j] = (LT / e.q + 1 + 31) / 32;  // a tile holds at most floor(L_tile/q)+1 multiples of q
     }
     if (tid == 0) {
         // distinct in-tile primes (their square is an in-tile prime power)
@@ -187,7 +190,7 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
 #pragma unroll
         for (int u = 0; u < kPer; u++) {
             const uint32_t j = lane * kPer + u;
-            v[u] = j < nspp ? (LT / sq[j] + 1 + 31) / 32 : 0;
+            v[u] = j < nspp ? (srounds[j] + kRoundsPerEntry - 1) / kRoundsPerEntry : 0;
             sum += v[u];
         }
         uint32_t inc = sum;
@@ -262,10 +265,15 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
             for (uint32_t g = warp; g < nsched; g += nwarps) {
                 const uint32_t e = sched[g];
                 const uint32_t j = e & 255u;
-                const uint32_t x = soff[j] + (((e >> 8) << 5) + lane) * sq[j];
-                if (x <= tl) {
-                    if (W16) atomicAdd(&tile[x >> 1], slg[j] << ((x & 1) << 4));
-                    else atomicAdd(&tile[x], slg[j]);
+                const uint32_t r0 = (e >> 8) * kRoundsPerEntry;
+                const uint32_t q = sq[j];
+                const uint32_t reps = min(kRoundsPerEntry, srounds[j] - r0);
+                uint32_t x = soff[j] + ((r0 << 5) + lane) * q;
+                // q is odd and 32q even: the parity of x, hence the half-word, is fixed per lane
+                const uint32_t lg = W16 ? slg[j] << ((x & 1) << 4) : slg[j];
+#pragma unroll
+                for (uint32_t r = 0; r < kRoundsPerEntry; r++, x += 32 * q) {
+                    if (r < reps && x <= tl) atomicAdd(W16 ? &tile[x >> 1] : &tile[x], lg);
                 }
             }
             for (uint32_t e = tid; e < nbc; e += NT) {
@@ -302,27 +310,33 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
                     const uint32_t w = tile[4 * g + 4];
                     uint32_t mx;
                     uint32_t ss[G];
+                    bool logc;
                     if constexpr (W16) {
                         // packed pair sums: low half L(2k) + L(2k+1), high half L(2k+1) + L(2k+2)
                         const uint32_t p0 = v.x + __funnelshift_r(v.x, v.y, 16);
                         const uint32_t p1 = v.y + __funnelshift_r(v.y, v.z, 16);
                         const uint32_t p2 = v.z + __funnelshift_r(v.z, v.w, 16);
                         const uint32_t p3 = v.w + __funnelshift_r(v.w, w, 16);
-                        const uint32_t m2 = __vmaxu2(__vmaxu2(p0, p1), __vmaxu2(p2, p3));
-                        mx = max(m2 & 0xffffu, m2 >> 16);
+                        // a pair sum is below 2^15: adding 2^15 - T to its half-word sets bit 15
+                        // exactly when the sum reaches T, and never carries into the other half
+                        const uint32_t K = (0x8000u - (T32 < 0x8000u ? T32 : 0x8000u)) * 0x10001u;
+                        logc = (((p0 + K) | (p1 + K) | (p2 + K) | (p3 + K)) & 0x80008000u) != 0u;
                         ss[0] = p0 & 0xffffu; ss[1] = p0 >> 16; ss[2] = p1 & 0xffffu; ss[3] = p1 >> 16;
                         ss[4] = p2 & 0xffffu; ss[5] = p2 >> 16; ss[6] = p3 & 0xffffu; ss[7] = p3 >> 16;
+                        mx = 0;
                     } else {
                         ss[0] = v.x + v.y;
                         ss[1] = v.y + v.z;
                         ss[2] = v.z + v.w;
                         ss[3] = v.w + w;
                         mx = max(max(ss[0], ss[1]), max(ss[2], ss[3]));
+                        logc = mx >= T32;
                     }
                     const uint32_t n0 = (uint32_t)(t_lo + G * g);  // low 32 bits suffice modulo 2^M
                     // does [n0, n0 + G] hold a multiple of 2^M?
                     const bool hi2 = ((n0 + G) & (M2 - 1)) <= G;
-                    if (all_cand || mx >= T32 || hi2) {
+                    (void)mx;
+                    if (all_cand || logc || hi2) {
 #pragma unroll
                         for (uint32_t u = 0; u < G; u++) {
                             const uint32_t nl = n0 + u;
