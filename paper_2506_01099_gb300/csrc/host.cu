@@ -55,7 +55,7 @@ static uint64_t isqrt64(uint64_t x) {
 
 // ----------------------------------------------------------------- tune ----
 static void tune_defaults(bnx_tune *t) {
-    t->tile_log2 = 14;
+    t->tile_log2 = 15;
     t->seg_tiles = 8;
     t->threads = 256;
     t->ctas_per_sm = 0;

@@ -253,7 +253,7 @@ int bnx_autotune(bnx_ctx *c, const bnx_interval *iv, size_t k, int rounds, char 
     float best_ms = 0;
     int rc = time_of(best, &best_ms);
     if (rc) return rc;
-    const uint32_t tiles[] = {12, 13, 14};
+    const uint32_t tiles[] = {13, 14, 15};
     const uint32_t segt[] = {2, 4, 8, 16, 32};
     const uint32_t thr[] = {128, 256, 512, 1024};
     const uint32_t qs[] = {12, 13, 14, 15, 16};
