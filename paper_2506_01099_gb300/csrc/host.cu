@@ -65,7 +65,6 @@ static void tune_defaults(bnx_tune *t) {
 
 static int tune_check(const bnx_tune *t) {
     if (t->tile_log2 < 10 || t->tile_log2 > 15) return fail(BNX_E_ARG, "tile_log2 must be in [10, 15]");
-    if (t->tile_log2 == 15 && t->tile_kind != 2) return fail(BNX_E_ARG, "tile_log2 = 15 needs tile_kind 2");
     if (t->seg_tiles < 1 || t->seg_tiles > 64 || (t->seg_tiles & (t->seg_tiles - 1)))
         return fail(BNX_E_ARG, "seg_tiles must be a power of two in [1, 64]");
     if (t->threads != 128 && t->threads != 256 && t->threads != 512 && t->threads != 1024)
@@ -287,14 +286,22 @@ Plan make_plan(const bnx_ctx *c) {
 // Launch shape of the persistent sieve for the current tuning (queried outside
 // any stream capture and cached until the tuning changes).
 static bool use_log_tile(const bnx_ctx *c, int mode) { return mode != kModeRad && c->tune.tile_kind != kTileExact; }
+
+// The exact u64 tile fits shared memory up to 2^14 values; a longer tuned tile
+// is processed by it as several tiles of the same queue segment.
+static uint32_t tile_log2_for(const bnx_ctx *c, int mode) {
+    return use_log_tile(c, mode) ? c->tune.tile_log2 : std::min<uint32_t>(c->tune.tile_log2, 14u);
+}
 static bool use_w16(const bnx_ctx *c) { return c->tune.tile_kind == kTileLog16; }
 
 int sieve_config(bnx_ctx *c, int mode, int *grid, int *threads, size_t *smem) {
     const bool lg = use_log_tile(c, mode), w16 = lg && use_w16(c);
     SieveCfg &sc = c->sieve_cfg[mode * 3 + (lg ? (w16 ? 2 : 1) : 0)];
-    const size_t want_smem = lg ? sieve_log_smem_bytes(c->tune.tile_log2, c->n_spp, c->n_sched(), w16)
-                                : sieve_smem_bytes(c->tune.tile_log2, c->n_spp, c->n_sched());
-    if (!sc.valid || sc.tile_log2 != c->tune.tile_log2 || sc.threads != c->tune.threads ||
+    const uint32_t tlog = tile_log2_for(c, mode);
+    const uint32_t nsched = sched_length(tlog, c->h_spp_q.data(), c->n_spp);
+    const size_t want_smem = lg ? sieve_log_smem_bytes(tlog, c->n_spp, nsched, w16)
+                                : sieve_smem_bytes(tlog, c->n_spp, nsched);
+    if (!sc.valid || sc.tile_log2 != tlog || sc.threads != c->tune.threads ||
         sc.ctas != c->tune.ctas_per_sm || sc.smem != want_smem) {
         if (c->capturing) return fail(BNX_E_STATE, "sieve launch shape unknown during capture");
         const int thr = (int)c->tune.threads;
@@ -307,7 +314,7 @@ int sieve_config(bnx_ctx *c, int mode, int *grid, int *threads, size_t *smem) {
         sc.grid = c->n_sm * per;
         sc.threads = c->tune.threads;
         sc.smem = smem_b;
-        sc.tile_log2 = c->tune.tile_log2;
+        sc.tile_log2 = tlog;
         sc.ctas = c->tune.ctas_per_sm;
         sc.occ = occ;
         sc.valid = true;
@@ -321,6 +328,8 @@ int sieve_config(bnx_ctx *c, int mode, int *grid, int *threads, size_t *smem) {
 // Launch the whole pipeline on stream s (directly or under capture).
 int record_pipeline(bnx_ctx *c, int mode, cudaStream_t s, bool timing) {
     Plan P = make_plan(c);
+    P.tile_log2 = tile_log2_for(c, mode);
+    P.n_sched = sched_length(P.tile_log2, c->h_spp_q.data(), c->n_spp);
     int sgrid, sthreads;
     size_t ssmem;
     int rc = sieve_config(c, mode, &sgrid, &sthreads, &ssmem);
