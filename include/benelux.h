@@ -182,6 +182,18 @@ int bnx_search(bnx_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t kinds, bnx_pair 
  * `out` is a HOST buffer.  Blocking.  Errors as bnx_search. */
 int bnx_search_hash(bnx_ctx *ctx, uint64_t S, uint32_t kinds, bnx_pair *out, size_t cap, size_t *n_out);
 
+/* Algorithm 3 (Sec. 2.2) as the paper runs it, kept as a measured baseline:
+ * all pairs with m < n < S by chunks of 2^chunk_log2 integers.  For each chunk
+ * C_i every n's key {rad n, rad n+1} goes into an open-addressing table of
+ * 4 * 2^chunk_log2 slots (collisions inside C_i give pairs), then every earlier
+ * chunk C_j is sieved again and probed (collisions give the pairs m in C_j,
+ * n in C_i): (S / 2^chunk_log2)^2 / 2 chunk sieves.  2 <= S <= 2^32 (keys
+ * are exact 64-bit words), S < max_hi, 10 <= chunk_log2 <= 28, kinds 1..3.
+ * The table and radical buffers are allocated for the call and freed after
+ * it.  `out` is a HOST buffer; blocking.  Errors as bnx_search. */
+int bnx_search_chunked(bnx_ctx *ctx, uint64_t S, uint32_t chunk_log2, uint32_t kinds, bnx_pair *out, size_t cap,
+                       size_t *n_out);
+
 /* Batched path: k intervals in one pipeline -- large-prime bucket fill, one
  * persistent sieve launch pulling segments from a device queue, verification
  * and a device sort -- replayed from a cached CUDA graph when the batch shape

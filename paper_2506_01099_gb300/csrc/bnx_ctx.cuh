@@ -113,4 +113,6 @@ int check_counters(bnx_ctx *c, bool *rerun);
 void fill_stats(bnx_ctx *c, uint64_t integers);
 int validate_interval(const bnx_ctx *c, uint64_t lo, uint64_t hi, uint32_t kinds);
 int search_staged(bnx_ctx *c, size_t k, bnx_pair *out, size_t cap, size_t *n_out, uint64_t *offsets);
+int rad_segment_unlocked(bnx_ctx *c, uint64_t lo, uint64_t len, uint64_t *rad_out, uint64_t *sq_out,
+                         cudaStream_t s);
 }  // namespace bnx

@@ -132,7 +132,8 @@ void launch_compact_primes(const uint8_t *comp, uint64_t lim, const uint32_t *bl
 void launch_exclusive_scan_u32(const uint32_t *in, unsigned long long *out, const unsigned long long *n_dev,
                                uint64_t n_cap, unsigned long long *tmp, uint32_t tmp_cap, cudaStream_t s);
 void launch_build_pp(const uint32_t *primes, uint32_t np, uint64_t max_hi, uint32_t q_small, SmallPP *spp,
-                     uint32_t *n_spp, LargePP *lpp, uint32_t *n_lpp, uint64_t lpp_cap, cudaStream_t s);
+                     uint32_t *n_spp, LargePP *lpp, uint32_t *n_lpp, uint64_t lpp_cap, uint32_t *scratch,
+                     cudaStream_t s);
 // sort lpp[0 .. n_pow2) by q (entries beyond the table hold q = 2^64 - 1)
 void launch_sort_lpp(LargePP *lpp, uint32_t n_valid, uint32_t n_pow2, cudaStream_t s);
 

@@ -110,10 +110,11 @@ int build_pp_tables(bnx_ctx *c) {
     int rc;
     if ((rc = grow(c->spp, sizeof(SmallPP) * kMaxSpp))) return rc;
     if ((rc = grow(c->lpp, sizeof(LargePP) * lpp_cap))) return rc;
-    if ((rc = grow(c->tmp_counts, sizeof(uint32_t) * 4))) return rc;
+    if ((rc = grow(c->tmp_counts, sizeof(uint32_t) * (4 + 4 * ((size_t)c->np + 1))))) return rc;
     uint32_t *cnt = (uint32_t *)c->tmp_counts.p;
     launch_build_pp((uint32_t *)c->primes.p, c->np, c->max_hi, q_small, (SmallPP *)c->spp.p, cnt,
-                    (LargePP *)c->lpp.p, cnt + 1, lpp_cap, c->stream);
+                    (LargePP *)c->lpp.p, cnt + 1, lpp_cap, cnt + 4, c->stream);
+    CUDA_TRY(cudaGetLastError());
     uint32_t h[2];
     CUDA_TRY(cudaMemcpyAsync(h, cnt, sizeof h, cudaMemcpyDeviceToHost, c->stream));
     CUDA_TRY(cudaStreamSynchronize(c->stream));
@@ -608,7 +609,15 @@ int bnx_rad_segment(bnx_ctx *c, uint64_t lo, uint64_t len, uint64_t *rad_out, ui
     if (c->server_running()) return fail(BNX_E_STATE, "the serving loop owns the context");
     std::lock_guard<std::mutex> g(c->mu);
     cudaSetDevice(c->device);
-    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    return rad_segment_unlocked(c, lo, len, rad_out, sq_out, stream ? (cudaStream_t)stream : c->stream);
+}
+
+}  // extern "C"
+
+namespace bnx {
+// bnx_rad_segment's work, for callers that already hold the context.
+int rad_segment_unlocked(bnx_ctx *c, uint64_t lo, uint64_t len, uint64_t *rad_out, uint64_t *sq_out,
+                         cudaStream_t s) {
     IvDev iv;
     memset(&iv, 0, sizeof iv);
     iv.lo = lo;
@@ -631,6 +640,9 @@ int bnx_rad_segment(bnx_ctx *c, uint64_t lo, uint64_t len, uint64_t *rad_out, ui
     c->rad_out = c->sq_out = nullptr;
     return rc;
 }
+}  // namespace bnx
+
+extern "C" {
 
 int bnx_search(bnx_ctx *c, uint64_t lo, uint64_t hi, uint32_t kinds, bnx_pair *out, size_t cap, size_t *n_out) {
     if (!c) return fail(BNX_E_ARG, "NULL context");

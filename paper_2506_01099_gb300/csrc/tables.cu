@@ -80,43 +80,56 @@ __global__ void k_compact_primes(const uint8_t *comp, uint64_t n, const uint32_t
     }
 }
 
-// One thread lists the odd prime powers: q = p^k, k >= 2.  q <= q_small goes
-// to the in-tile table (at most kMaxSpp entries), q_small < q <= max_hi to the
-// bucket table.  Order: by p, then k.
-__global__ void k_build_pp(const uint32_t *primes, uint32_t np, uint64_t max_hi, uint32_t q_small, SmallPP *spp,
-                           uint32_t *n_spp, LargePP *lpp, uint32_t *n_lpp, uint64_t lpp_cap) {
-    if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    uint32_t ns = 0;
-    uint64_t nl = 0;
-    for (uint32_t i = 0; i < np; i++) {
-        uint64_t p = primes[i];
-        if (p == 2) continue;  // the prime 2 is handled by counting trailing zeros
-        if (p * p > max_hi) break;
+// The odd prime powers q = p^k, k >= 2, q <= max_hi: those <= q_small go to the
+// in-tile table (ordered by p, then k; at most kMaxSpp entries), the larger ones
+// to the bucket table.  One thread per prime counts its powers of each class;
+// exclusive scans of the counts give every prime its output positions; a second
+// pass writes the entries.
+__device__ __forceinline__ void pp_counts(uint64_t p, uint64_t max_hi, uint32_t q_small, uint32_t *ns, uint32_t *nl) {
+    *ns = 0;
+    *nl = 0;
+    if (p == 2 || p * p > max_hi) return;  // the prime 2 is handled by counting trailing zeros
+    for (uint64_t q = p * p;; q *= p) {
+        if (q <= q_small) (*ns)++;
+        else (*nl)++;
+        if (q > max_hi / p) break;
+    }
+}
+
+__global__ void k_pp_count(const uint32_t *primes, uint32_t np, uint64_t max_hi, uint32_t q_small, uint32_t *cs,
+                           uint32_t *cl) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x)
+        pp_counts(primes[i], max_hi, q_small, &cs[i], &cl[i]);
+}
+
+__global__ void k_pp_write(const uint32_t *primes, uint32_t np, uint64_t max_hi, uint32_t q_small,
+                           const uint32_t *os, const uint32_t *ol, SmallPP *spp, LargePP *lpp, uint64_t lpp_cap) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
+        const uint64_t p = primes[i];
+        if (p == 2 || p * p > max_hi) continue;
         const uint32_t lg = (uint32_t)floor(log2((double)p) * (double)(1u << kLogFrac)) + 1u;
-        uint32_t e = 2;
+        uint32_t si = os[i], li = ol[i], e = 2;
         for (uint64_t q = p * p;; q *= p, e++) {
             if (q <= q_small) {
-                if (ns < kMaxSpp) {
-                    spp[ns].q = (uint32_t)q;
-                    spp[ns].p = (uint32_t)p;
-                    spp[ns].lg = lg;
-                    spp[ns].k = e;
+                if (si < kMaxSpp) {
+                    spp[si].q = (uint32_t)q;
+                    spp[si].p = (uint32_t)p;
+                    spp[si].lg = lg;
+                    spp[si].k = e;
                 }
-                ns++;
+                si++;
             } else {
-                if (nl < lpp_cap) {
-                    lpp[nl].q = q;
-                    lpp[nl].m = ~0ull / q;
-                    lpp[nl].p = (uint32_t)p;
-                    lpp[nl].pad = 0;
+                if (li < lpp_cap) {
+                    lpp[li].q = q;
+                    lpp[li].m = ~0ull / q;
+                    lpp[li].p = (uint32_t)p;
+                    lpp[li].pad = 0;
                 }
-                nl++;
+                li++;
             }
             if (q > max_hi / p) break;
         }
     }
-    *n_spp = ns;
-    *n_lpp = (uint32_t)nl;
 }
 
 // ---- bitonic sort of the large prime-power table by q (once per context) ----
@@ -256,8 +269,17 @@ void launch_compact_primes(const uint8_t *comp, uint64_t lim, const uint32_t *bl
 }
 
 void launch_build_pp(const uint32_t *primes, uint32_t np, uint64_t max_hi, uint32_t q_small, SmallPP *spp,
-                     uint32_t *n_spp, LargePP *lpp, uint32_t *n_lpp, uint64_t lpp_cap, cudaStream_t s) {
-    k_build_pp<<<1, 1, 0, s>>>(primes, np, max_hi, q_small, spp, n_spp, lpp, n_lpp, lpp_cap);
+                     uint32_t *n_spp, LargePP *lpp, uint32_t *n_lpp, uint64_t lpp_cap, uint32_t *scratch,
+                     cudaStream_t s) {
+    // scratch: 4 * (np + 1) u32 -- counts and offsets of both classes
+    uint32_t *cs = scratch, *cl = scratch + (np + 1), *os = scratch + 2 * (np + 1), *ol = scratch + 3 * (np + 1);
+    const int grid = (int)((np + 255) / 256 < 1024 ? (np + 255) / 256 + 1 : 1024);
+    k_pp_count<<<grid, 256, 0, s>>>(primes, np, max_hi, q_small, cs, cl);
+    cudaMemcpyAsync(os, cs, sizeof(uint32_t) * np, cudaMemcpyDeviceToDevice, s);
+    cudaMemcpyAsync(ol, cl, sizeof(uint32_t) * np, cudaMemcpyDeviceToDevice, s);
+    k_scan_small<<<1, 1024, 0, s>>>(os, np, n_spp);
+    k_scan_small<<<1, 1024, 0, s>>>(ol, np, n_lpp);
+    k_pp_write<<<grid, 256, 0, s>>>(primes, np, max_hi, q_small, os, ol, spp, lpp, lpp_cap);
 }
 
 void launch_exclusive_scan_u32(const uint32_t *in, unsigned long long *out, const unsigned long long *n_dev,

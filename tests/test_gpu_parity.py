@@ -254,3 +254,13 @@ def test_three_term_kind(ctx, orc):
     assert ctx.search(1, 1 << 32, 5) == theorem1_pairs(1, 1 << 32, 1)
     lo = 2**40 - 2**22
     assert ctx.search(lo, lo + 2**23, 6) == orc.pairs_crt(lo, lo + 2**23, 6)
+
+
+def test_algorithm3_chunked(ctx, orc):
+    """The paper's Algorithm 3 (all earlier chunks re-sieved and probed) finds the
+    same pairs as the oracle, with S not a multiple of the chunk."""
+    S = (1 << 20) + 12345
+    got = ctx.search_chunked(S, 16)
+    assert got == orc.pairs_sort(S)
+    assert ctx.search_chunked(1 << 22, 18, 2) == theorem1_pairs(1, 1 << 22, 2)
+    assert ctx.search_chunked(1 << 22, 18, 1) == theorem1_pairs(1, 1 << 22, 1)
