@@ -194,6 +194,22 @@ int bnx_search_hash(bnx_ctx *ctx, uint64_t S, uint32_t kinds, bnx_pair *out, siz
 int bnx_search_chunked(bnx_ctx *ctx, uint64_t S, uint32_t chunk_log2, uint32_t kinds, bnx_pair *out, size_t cap,
                        size_t *n_out);
 
+/* Algorithm 2 (Sec. 2.1) on the device: all pairs with m < n < S by sorting.
+ * The radicals of [1, S] are sieved, every n < S gets the exact key
+ * {rad n, rad n+1} = max << 32 | min, relabelled by a bijective 64-bit mix h,
+ * the (h, n) records are sorted by the top 32 bits of h (a stable 4-pass
+ * least-significant-digit radix sort), and every run of equal prefixes gives
+ * all its pairs m < n with equal h, i.e. equal 2-sets (not only neighbours, so
+ * runs of three or more lose nothing), of the first kind when rad(m) = rad(n).
+ * 3 <= S <= 2^32,
+ * S < max_hi, kinds 1..3.  About 32 S bytes of device memory (radicals and two
+ * key/value buffers) are allocated for the call and freed after it: 137 GB at
+ * S = 2^32.  `out` is a HOST buffer; blocking.  Errors as bnx_search,
+ * BNX_E_NOMEM when the buffers do not fit, and BNX_E_TIMEOUT if a tile of the
+ * sort waited too long for the counts of the tiles before it (a bounded wait
+ * that is not expected to run out). */
+int bnx_search_sorted(bnx_ctx *ctx, uint64_t S, uint32_t kinds, bnx_pair *out, size_t cap, size_t *n_out);
+
 /* Batched path: k intervals in one pipeline -- large-prime bucket fill, one
  * persistent sieve launch pulling segments from a device queue, verification
  * and a device sort -- replayed from a cached CUDA graph when the batch shape

@@ -85,6 +85,7 @@ def lib(auto_build: bool = True):
             "bnx_search": ([vp, u64, u64, u32, P(bnx_pair), sz, P(sz)], i32),
             "bnx_search_hash": ([vp, u64, u32, P(bnx_pair), sz, P(sz)], i32),
             "bnx_search_chunked": ([vp, u64, u32, u32, P(bnx_pair), sz, P(sz)], i32),
+            "bnx_search_sorted": ([vp, u64, u32, P(bnx_pair), sz, P(sz)], i32),
             "bnx_batch": ([vp, P(bnx_interval), sz, P(bnx_pair), sz, P(sz), P(u64)], i32),
             "bnx_server_start": ([vp, P(bnx_server_cfg)], i32),
             "bnx_server_submit": ([vp, P(bnx_interval), P(u64)], i32),
@@ -200,6 +201,12 @@ def bnx_search_chunked(ctx, S: int, chunk_log2: int = 27, kinds: int = 3):
     return _pairs(buf, n)
 
 
+def bnx_search_sorted(ctx, S: int, kinds: int = 3):
+    """Pairs (m, n, kind) with m < n < S by Algorithm 2 (device radix sort of the keys)."""
+    buf, n = _grow_call(lambda b, c, pn: lib().bnx_search_sorted(ctx, S, kinds, b, c, pn))
+    return _pairs(buf, n)
+
+
 def make_intervals(intervals):
     """Sequence of (lo, hi, kinds[, id]) or objects with .lo/.hi/.kinds -> ctypes array."""
     arr = (bnx_interval * max(1, len(intervals)))()
@@ -295,6 +302,9 @@ class Context:
 
     def search_chunked(self, S, chunk_log2=27, kinds=3):
         return bnx_search_chunked(self.h, S, chunk_log2, kinds)
+
+    def search_sorted(self, S, kinds=3):
+        return bnx_search_sorted(self.h, S, kinds)
 
     def batch(self, intervals):
         return bnx_batch(self.h, intervals)

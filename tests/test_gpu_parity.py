@@ -264,3 +264,27 @@ def test_algorithm3_chunked(ctx, orc):
     assert got == orc.pairs_sort(S)
     assert ctx.search_chunked(1 << 22, 18, 2) == theorem1_pairs(1, 1 << 22, 2)
     assert ctx.search_chunked(1 << 22, 18, 1) == theorem1_pairs(1, 1 << 22, 1)
+
+
+@pytest.mark.parametrize("S", [3, 4, 5, 100, 7169, 7168 * 3 + 17, 8192 * 3 + 17, (1 << 20) + 12345])
+def test_algorithm2_sorted(ctx, orc, S):
+    """The paper's Algorithm 2 by a device radix sort: the same pairs as the
+    oracle's sort-based search, with ragged last sort tiles and tiny S."""
+    assert ctx.search_sorted(S) == orc.pairs_sort(S)
+
+
+def test_algorithm2_sorted_kinds_and_scale(ctx, orc):
+    """Single kinds, and S = 2^30 (radix sort of 2^30 records over 149797 tiles)
+    against the pairs of Theorem 1."""
+    S = (1 << 22) + 3
+    both = orc.pairs_sort(S)
+    assert ctx.search_sorted(S, 1) == [p for p in both if p[2] == 1]
+    assert ctx.search_sorted(S, 2) == [p for p in both if p[2] == 2]
+    assert ctx.search_sorted(1 << 30) == theorem1_pairs(1, 1 << 30, 3)
+
+
+def test_algorithm2_sorted_bad_arguments(B, ctx):
+    for S, kinds in [(2, 3), ((1 << 32) + 1, 3), (1 << 20, 4), (1 << 20, 0)]:
+        with pytest.raises(B.BnxError) as e:
+            ctx.search_sorted(S, kinds)
+        assert e.value.code == B.BNX_E_ARG
