@@ -472,6 +472,17 @@ def profile_case(override: str | None = None):
     return 0
 
 
+def profile_sorted(lg: int):
+    """One Algorithm 2 search of all n < 2^lg (small case for ncu)."""
+    from paper_2506_01099_gb300 import benelux as B
+
+    ctx = B.Context(0, max_hi=MAX_HI)
+    pairs = ctx.search_sorted(1 << lg)
+    print(json.dumps({"profile_sorted": 1 << lg, "pairs": len(pairs), "stats": ctx.stats()}))
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -490,7 +501,11 @@ def main():
     ap.add_argument("--tune", default=None, help="JSON of bnx_tune fields applied over the cached tuning")
     ap.add_argument("--profile-case", action="store_true",
                     help="one warm-up and one search of [2^40, 2^40 + 2^28) (small case for ncu), then exit")
+    ap.add_argument("--profile-sorted", type=int, default=0, metavar="LG",
+                    help="one Algorithm 2 search of all n < 2^LG (small case for ncu), then exit")
     args = ap.parse_args()
+    if args.profile_sorted:
+        return profile_sorted(args.profile_sorted)
     if args.profile_case:
         return profile_case(args.tune)
     if args.impl == "reference":
