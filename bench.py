@@ -210,6 +210,22 @@ def cpu_baseline(intervals, budget_integers: int):
             "seconds": dt, "pairs": npairs}
 
 
+def cpu_full_ranges():
+    """The oracle on the two full-range searches, all n < 2^24 and all n < 2^32
+    (both kinds), on the host cores: the CPU side of the full-range GPU timings."""
+    import oracle
+
+    orc = oracle.load()
+    out = {"cores": os.cpu_count() or 1}
+    for name, S in (("n_below_2p24", 1 << 24), ("n_below_2p32", 1 << 32)):
+        orc.lib.orc_init(2 * S + 2)
+        t0 = time.perf_counter()
+        pairs = orc.pairs_crt(1, S, 3)
+        out[name] = {"seconds": time.perf_counter() - t0, "pairs": len(pairs),
+                     "method": "CRT enumeration over Algorithm 1 radicals (orc_pairs_crt)"}
+    return out
+
+
 # ---------------------------------------------------------------------------
 
 def run_reference(args):
@@ -332,6 +348,7 @@ def run_ours(args):
                             "pairs_plain": [list(p) for p in p_plain],
                             "pairs_batched": [list(p[1:]) for p in p_b]}
         extras["full_range_2p32"] = full_range_2p32(ctx)
+        extras["materialised_rad"] = materialised_rad(ctx, torch, stream)
         extras["serving"] = serve_stream(B, ctx, args, throughput=value / ws)
         extras["serving_saturated"] = serve_stream(B, ctx, args, throughput=value / ws, saturate=True)
 
@@ -344,6 +361,8 @@ def run_ours(args):
         cpu = None
         if not args.no_cpu and ws == 1:
             cpu = cpu_baseline(W.batch_intervals(4096), int(args.cpu_budget))
+            if not args.quick:
+                cpu["full_ranges"] = cpu_full_ranges()
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
@@ -406,6 +425,30 @@ def full_range_2p32(ctx):
         out[name] = {"seconds": dt, "pairs": len(pairs), "device_ms": ctx.stats()["ms_total"]}
     out["note"] = "paper: about one minute for n < 2^32 with Algorithm 3 on a 2021 consumer GPU"
     return out
+
+
+def materialised_rad(ctx, torch, stream):
+    """The HBM-writing counterpoint to the fused search: bnx_rad_segment writes
+    the radical and the square part of each of the 2^31 integers
+    [2^40, 2^40 + 2^31) to HBM (16 B per integer), CUDA-event timed."""
+    lo, n = 1 << 40, 1 << 31
+    rad = torch.empty(n, dtype=torch.int64, device="cuda")
+    sq = torch.empty(n, dtype=torch.int64, device="cuda")
+    ctx.rad_segment(lo, n, rad.data_ptr(), sq.data_ptr(), stream.cuda_stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ctx.rad_segment(lo, n, rad.data_ptr(), sq.data_ptr(), stream.cuda_stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    check = int(rad[0].item()) == 2 and int(sq[0].item()) == 1 << 39  # 2^40: radical 2
+    del rad, sq
+    torch.cuda.empty_cache()
+    hbm = float(peaks()[0].get("hbm_gbs", 6800.0))
+    gbs = 16 * n / (ms / 1e3) / 1e9
+    return {"range": [lo, lo + n], "integers_per_s": n / (ms / 1e3), "ms": ms, "written_GBps": gbs,
+            "hbm_frac": gbs / hbm, "first_value_ok": check,
+            "note": "exact u64 tile sieve writing rad and the square part; the fused search writes neither"}
 
 
 def serve_stream(B, ctx, args, throughput: float, saturate: bool = False):

@@ -25,7 +25,14 @@ namespace bnx {
 
 namespace {
 
-constexpr int kLogBucketCache = 256;
+// A segment's bucket entries are cached in shared memory, each packed into one
+// word: (offset in the segment) << 12 | lg7, lg7 = ceil(log2 p * 2^7) with
+// margin (p < 2^22: lg7 < 2^12).  Offsets reach the segment length, so the
+// cache is used for segments of at most 2^19 values; larger segments read all
+// their entries from global memory.  A strike
+// adds lg7 << 1 to the u16 tile (units 2^-8) or lg7 << 9 to the u32 tile
+// (units 2^-16): an over-estimate of log2 p, as the rejection rule needs.
+constexpr int kLogBucketCache = 1024;
 constexpr uint32_t kHigh2 = 16;
 constexpr int kMaxSmallPrimes = 64;
 constexpr uint32_t kRoundsPerEntry = 4;  // a schedule entry strikes up to 4 x 32 multiples of one q
@@ -46,7 +53,7 @@ __device__ __forceinline__ uint32_t find_iv(const IvDev *ivs, uint32_t k, uint64
 }
 
 struct LogLayout {
-    size_t tile, spp, sched, bcache, blg, total;
+    size_t tile, spp, sched, bcache, total;
 };
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -60,8 +67,7 @@ __host__ __device__ inline LogLayout log_layout(uint32_t tile_log2, uint32_t nsp
     L.spp = al16(words * sizeof(uint32_t));
     L.sched = L.spp + al16((size_t)5 * (nspp ? nspp : 1) * sizeof(uint32_t));
     L.bcache = L.sched + al16((size_t)(nsched ? nsched : 1) * sizeof(uint16_t));
-    L.blg = L.bcache + (size_t)kLogBucketCache * sizeof(uint2);
-    L.total = L.blg + (size_t)kLogBucketCache * sizeof(uint32_t);
+    L.total = L.bcache + (size_t)kLogBucketCache * sizeof(uint32_t);
     return L;
 }
 
@@ -72,6 +78,8 @@ __device__ __forceinline__ uint32_t lg_large(uint32_t p) {
 }
 // the same in units of 2^-8 (u16 tile); 2 units cover the error and the truncation
 __device__ __forceinline__ uint32_t lg_large8(uint32_t p) { return __float2uint_rd(log2f((float)p) * 256.0f) + 2u; }
+// a bucket entry packed for the shared cache (units of 2^-7, rounded up from lg_large8)
+__device__ __forceinline__ uint32_t pack_hit(uint2 h) { return (h.x << 12) | ((lg_large8(h.y) + 1u) >> 1); }
 
 struct SmallPrimes {
     uint32_t n;
@@ -82,8 +90,7 @@ struct SmallPrimes {
 
 // exact odd square part of the value v at offset o of its segment
 __device__ __noinline__ uint64_t sodd_exact(uint64_t v, uint32_t o, const SmallPrimes *sp, uint32_t sqrt_q,
-                                            const uint2 *bc, uint32_t nbc, const uint2 *bent, unsigned long long gb,
-                                            unsigned long long ge) {
+                                            const uint2 *bent, unsigned long long gb, unsigned long long ge) {
     uint64_t y = v >> ctz64(v);
     uint64_t s = 1;
     for (uint32_t t = 0; t < sp->n; t++) {
@@ -96,8 +103,6 @@ __device__ __noinline__ uint64_t sodd_exact(uint64_t v, uint32_t o, const SmallP
             }
         }
     }
-    for (uint32_t e = 0; e < nbc; e++)
-        if (bc[e].x == o && bc[e].y > sqrt_q) s *= bc[e].y;
     for (unsigned long long e = gb; e < ge; e++) {
         const uint2 h = bent[e];
         if (h.x == o && h.y > sqrt_q) s *= h.y;
@@ -149,8 +154,7 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
     uint32_t *slmod = soff + nspp;
     uint32_t *srounds = slmod + nspp;  // 32-multiple rounds of q in a tile
     uint16_t *sched = reinterpret_cast<uint16_t *>(smem_raw + lay.sched);
-    uint2 *bcache = reinterpret_cast<uint2 *>(smem_raw + lay.bcache);
-    uint32_t *blg = reinterpret_cast<uint32_t *>(smem_raw + lay.blg);
+    uint32_t *bcache = reinterpret_cast<uint32_t *>(smem_raw + lay.bcache);
     __shared__ SmallPrimes sprimes;
     __shared__ unsigned long long s_seg;
     __shared__ uint32_t s_iv, s_nsched;
@@ -223,18 +227,14 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
         const uint64_t rem = iv.hi - seg_lo;
         const uint32_t seg_len = rem < (1ull << P.seg_log2) ? (uint32_t)rem : (1u << P.seg_log2);
         const unsigned long long b0 = P.boff[seg], b1 = P.boff[seg + 1];
-        const uint32_t nbc =
-            (uint32_t)((b1 - b0) < (unsigned long long)kLogBucketCache ? (b1 - b0) : kLogBucketCache);
+        const unsigned long long ncache = P.seg_log2 <= 19 ? (unsigned long long)kLogBucketCache : 0ull;
+        const uint32_t nbc = (uint32_t)((b1 - b0) < ncache ? (b1 - b0) : ncache);
         for (uint32_t j = tid; j < nspp; j += NT) {
             const uint32_t q = sq[j];
             const uint32_t r = (uint32_t)(seg_lo % q);
             soff[j] = r ? q - r : 0;
         }
-        for (uint32_t e = tid; e < nbc; e += NT) {
-            const uint2 h = P.bent[b0 + e];
-            bcache[e] = h;
-            blg[e] = W16 ? lg_large8(h.y) : lg_large(h.y);
-        }
+        for (uint32_t e = tid; e < nbc; e += NT) bcache[e] = pack_hit(P.bent[b0 + e]);
         const uint32_t nsched = s_nsched;
         const uint32_t kinds = iv.kinds;
 
@@ -277,14 +277,14 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
                 }
             }
             for (uint32_t e = tid; e < nbc; e += NT) {
-                const uint2 h = bcache[e];
-                if (h.x >= t0 && h.x <= t0 + tl) {
-                    const uint32_t x = h.x - t0;
-                    if (W16) atomicAdd(&tile[x >> 1], blg[e] << ((x & 1) << 4));
-                    else atomicAdd(&tile[x], blg[e]);
+                const uint32_t w = bcache[e];
+                const uint32_t x = (w >> 12) - t0;  // wraps to a large value below t0
+                if (x <= tl) {
+                    if (W16) atomicAdd(&tile[x >> 1], (w & 0xfffu) << (1 + ((x & 1) << 4)));
+                    else atomicAdd(&tile[x], (w & 0xfffu) << 9);
                 }
             }
-            for (unsigned long long e = b0 + kLogBucketCache + tid; e < b1; e += NT) {
+            for (unsigned long long e = b0 + nbc + tid; e < b1; e += NT) {
                 const uint2 h = P.bent[e];
                 if (h.x >= t0 && h.x <= t0 + tl) {
                     const uint32_t x = h.x - t0;
@@ -366,10 +366,8 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
                                    ((S2 & (S2 - 1)) ? 1 : 0);
                         }
                         if (ub >= (int64_t)need * FS) {
-                            const uint64_t s0 = sodd_exact(n, t0 + i, &sprimes, P.sqrt_q, bcache, nbc, P.bent,
-                                                           b0 + kLogBucketCache, b1);
-                            const uint64_t s1 = sodd_exact(n + 1, t0 + i + 1, &sprimes, P.sqrt_q, bcache, nbc,
-                                                           P.bent, b0 + kLogBucketCache, b1);
+                            const uint64_t s0 = sodd_exact(n, t0 + i, &sprimes, P.sqrt_q, P.bent, b0, b1);
+                            const uint64_t s1 = sodd_exact(n + 1, t0 + i + 1, &sprimes, P.sqrt_q, P.bent, b0, b1);
                             kk = exact_kinds_log(n, s0, s1, kinds, MODE, P.hash_S, &a, &b);
                         }
                     }

@@ -86,7 +86,13 @@ def test_rad_segment_large_sampled(ctx, orc):
                                   dict(tile_kind=2, tile_log2=13, threads=128, small_q_log2=16),
                                   dict(tile_kind=2, tile_log2=14, threads=512, seg_tiles=2, small_q_log2=10),
                                   dict(tile_kind=1, tile_log2=15, seg_tiles=2),
-                                  dict(tile_kind=0, tile_log2=15, threads=1024)])
+                                  dict(tile_kind=0, tile_log2=15, threads=1024),
+                                  # 2^19-value segments (the packed bucket cache at its offset limit) with
+                                  # Q = 2^8: far more entries than the 1024 cached ones
+                                  dict(tile_kind=2, tile_log2=15, seg_tiles=16, small_q_log2=8),
+                                  # 2^20-value segments: the cache is off, every entry read from HBM
+                                  dict(tile_kind=2, tile_log2=15, seg_tiles=32),
+                                  dict(tile_kind=0, tile_log2=14, seg_tiles=64, small_q_log2=9)])
 def test_tunings_agree(B, orc, tune):
     with B.Context(0, max_hi=1 << 41) as c:
         c.set_tune(**tune)
