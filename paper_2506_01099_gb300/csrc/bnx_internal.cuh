@@ -79,6 +79,7 @@ constexpr unsigned kErrSurvOverflow = 1u;
 constexpr unsigned kErrPairOverflow = 2u;
 constexpr unsigned kErrBucketOverflow = 4u;
 constexpr unsigned kErrHashFull = 8u;
+constexpr unsigned kErrSchedule = 32u;  // a strike schedule did not fit its array (never expected)
 
 // Everything a pipeline's kernels read.  Passed by value to every launch; the
 // sizes that vary per run live in device memory (Counters, IvDev) so that one

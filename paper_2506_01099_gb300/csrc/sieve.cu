@@ -509,9 +509,15 @@ const void *sieve_fn(int mode, int threads) {
 
 }  // namespace
 
+// Words of the strike schedule: the exact tile needs one per round of 32
+// multiples of each q; the log-domain tile needs fewer for q with several
+// rounds, and floor(L/q) + 1 slots for q with a single round.
 uint32_t sched_length(uint32_t tile_log2, const uint32_t *q, uint32_t nspp) {
     uint32_t n = 0;
-    for (uint32_t j = 0; j < nspp; j++) n += (((1u << tile_log2) / q[j]) + 1 + 31) / 32;
+    for (uint32_t j = 0; j < nspp; j++) {
+        const uint32_t mult = ((1u << tile_log2) / q[j]) + 1, rounds = (mult + 31) / 32;
+        n += rounds == 1 ? mult : rounds;
+    }
     return n;
 }
 

@@ -157,7 +157,7 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
     uint32_t *bcache = reinterpret_cast<uint32_t *>(smem_raw + lay.bcache);
     __shared__ SmallPrimes sprimes;
     __shared__ unsigned long long s_seg;
-    __shared__ uint32_t s_iv, s_nsched;
+    __shared__ uint32_t s_iv, s_nsched, s_nsparse;
 
     const uint32_t tid = threadIdx.x;
     const uint32_t lane = tid & 31, warp = tid >> 5;
@@ -187,30 +187,55 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
         sprimes.inv[t] = inv;
         sprimes.lim[t] = ~0ull / p;
     }
+    // Static strike schedule.  A prime power with at least two rounds of 32
+    // multiples per tile gets entries (j, c) of up to kRoundsPerEntry rounds
+    // each, a warp striking 32 consecutive multiples per round.  One with a
+    // single round (at most 32 multiples) gets one slot (j, m) per possible
+    // multiple m, and the slots of all of them are packed 32 to a warp pass, so
+    // that a warp pass is not spent on a handful of strikes.  The slots follow
+    // the entries in `sched`.
     if (warp == 0) {
         constexpr int kPer = kMaxSpp / 32;
-        uint32_t v[kPer];
-        uint32_t sum = 0;
-#pragma unroll
+        // entries (v) and slots (w) of prime power j
+        auto counts = [&](uint32_t j, uint32_t &v, uint32_t &w) {
+            const bool single = j < nspp && srounds[j] == 1;
+            v = j < nspp && !single ? (srounds[j] + kRoundsPerEntry - 1) / kRoundsPerEntry : 0;
+            w = single ? LT / sq[j] + 1 : 0;  // at most 32
+        };
+        uint32_t sum = 0, sumw = 0;
         for (int u = 0; u < kPer; u++) {
-            const uint32_t j = lane * kPer + u;
-            v[u] = j < nspp ? (srounds[j] + kRoundsPerEntry - 1) / kRoundsPerEntry : 0;
-            sum += v[u];
+            uint32_t v, w;
+            counts(lane * kPer + u, v, w);
+            sum += v;
+            sumw += w;
         }
-        uint32_t inc = sum;
+        uint32_t inc = sum, incw = sumw;
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t x = __shfl_up_sync(0xffffffffu, inc, o);
-            if (lane >= (uint32_t)o) inc += x;
+            const uint32_t y = __shfl_up_sync(0xffffffffu, incw, o);
+            if (lane >= (uint32_t)o) {
+                inc += x;
+                incw += y;
+            }
         }
-        uint32_t run = inc - sum;
-#pragma unroll
+        const uint32_t ndense = __shfl_sync(0xffffffffu, inc, 31);
+        uint32_t run = inc - sum, runw = ndense + incw - sumw;
         for (int u = 0; u < kPer; u++) {
             const uint32_t j = lane * kPer + u;
-            for (uint32_t c = 0; c < v[u]; c++)
+            uint32_t v, w;
+            counts(j, v, w);
+            for (uint32_t c = 0; c < v; c++)
                 if (run + c < P.n_sched) sched[run + c] = (uint16_t)(j | (c << 8));
-            run += v[u];
+            for (uint32_t m = 0; m < w; m++)
+                if (runw + m < P.n_sched) sched[runw + m] = (uint16_t)(j | (m << 8));
+            run += v;
+            runw += w;
         }
-        if (lane == 31) s_nsched = inc < P.n_sched ? inc : P.n_sched;
+        if (lane == 31) {
+            s_nsched = inc < P.n_sched ? inc : P.n_sched;
+            s_nsparse = ndense + incw <= P.n_sched ? incw : 0u;  // n_sched always covers both
+            if (ndense + incw > P.n_sched && blockIdx.x == 0) atomicOr(&P.ctr->err, kErrSchedule);
+        }
     }
 
     for (;;) {
@@ -235,7 +260,8 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
             soff[j] = r ? q - r : 0;
         }
         for (uint32_t e = tid; e < nbc; e += NT) bcache[e] = pack_hit(P.bent[b0 + e]);
-        const uint32_t nsched = s_nsched;
+        const uint32_t nsched = s_nsched, nsparse = s_nsparse;
+        const uint32_t nwork = nsched + (nsparse + 31) / 32;
         const uint32_t kinds = iv.kinds;
 
         for (uint32_t t0 = 0; t0 < seg_len; t0 += LT) {
@@ -262,18 +288,28 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
                 for (uint32_t i = tid; i < n4; i += NT) t4[i] = z;
             }
             __syncthreads();
-            for (uint32_t g = warp; g < nsched; g += nwarps) {
-                const uint32_t e = sched[g];
-                const uint32_t j = e & 255u;
-                const uint32_t r0 = (e >> 8) * kRoundsPerEntry;
-                const uint32_t q = sq[j];
-                const uint32_t reps = min(kRoundsPerEntry, srounds[j] - r0);
-                uint32_t x = soff[j] + ((r0 << 5) + lane) * q;
-                // q is odd and 32q even: the parity of x, hence the half-word, is fixed per lane
-                const uint32_t lg = W16 ? slg[j] << ((x & 1) << 4) : slg[j];
+            for (uint32_t g = warp; g < nwork; g += nwarps) {
+                if (g < nsched) {
+                    const uint32_t e = sched[g];
+                    const uint32_t j = e & 255u;
+                    const uint32_t r0 = (e >> 8) * kRoundsPerEntry;
+                    const uint32_t q = sq[j];
+                    const uint32_t reps = min(kRoundsPerEntry, srounds[j] - r0);
+                    uint32_t x = soff[j] + ((r0 << 5) + lane) * q;
+                    // q is odd and 32q even: the parity of x, hence the half-word, is fixed per lane
+                    const uint32_t lg = W16 ? slg[j] << ((x & 1) << 4) : slg[j];
 #pragma unroll
-                for (uint32_t r = 0; r < kRoundsPerEntry; r++, x += 32 * q) {
-                    if (r < reps && x <= tl) atomicAdd(W16 ? &tile[x >> 1] : &tile[x], lg);
+                    for (uint32_t r = 0; r < kRoundsPerEntry; r++, x += 32 * q) {
+                        if (r < reps && x <= tl) atomicAdd(W16 ? &tile[x >> 1] : &tile[x], lg);
+                    }
+                } else {  // packed slots of the single-round prime powers
+                    const uint32_t sl = (g - nsched) * 32 + lane;
+                    if (sl < nsparse) {
+                        const uint32_t e = sched[nsched + sl];
+                        const uint32_t j = e & 255u;
+                        const uint32_t x = soff[j] + (e >> 8) * sq[j];
+                        if (x <= tl) atomicAdd(W16 ? &tile[x >> 1] : &tile[x], W16 ? slg[j] << ((x & 1) << 4) : slg[j]);
+                    }
                 }
             }
             for (uint32_t e = tid; e < nbc; e += NT) {
