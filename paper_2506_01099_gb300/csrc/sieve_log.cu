@@ -148,11 +148,9 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
     const uint32_t nspp = P.n_spp;
     const LogLayout lay = log_layout(tile_log2, nspp, P.n_sched, W16);
     uint32_t *tile = reinterpret_cast<uint32_t *>(smem_raw + lay.tile);
-    uint32_t *sq = reinterpret_cast<uint32_t *>(smem_raw + lay.spp);
-    uint32_t *slg = sq + nspp;
-    uint32_t *soff = slg + nspp;
-    uint32_t *slmod = soff + nspp;
-    uint32_t *srounds = slmod + nspp;  // 32-multiple rounds of q in a tile
+    // per in-tile prime power j: {q, lg, offset of its first multiple in the tile, 32-multiple rounds per tile}
+    uint4 *sdesc = reinterpret_cast<uint4 *>(smem_raw + lay.spp);
+    uint32_t *slmod = reinterpret_cast<uint32_t *>(sdesc + nspp);  // L_tile mod q
     uint16_t *sched = reinterpret_cast<uint16_t *>(smem_raw + lay.sched);
     uint32_t *bcache = reinterpret_cast<uint32_t *>(smem_raw + lay.bcache);
     __shared__ SmallPrimes sprimes;
@@ -167,10 +165,9 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
 
     for (uint32_t j = tid; j < nspp; j += NT) {
         const SmallPP e = P.spp[j];
-        sq[j] = e.q;
-        slg[j] = W16 ? (uint32_t)floor(log2((double)e.p) * 256.0) + 1u : e.lg;
+        sdesc[j] = make_uint4(e.q, W16 ? (uint32_t)floor(log2((double)e.p) * 256.0) + 1u : e.lg, 0u,
+                              (LT / e.q + 1 + 31) / 32);  // a tile holds at most floor(L_tile/q)+1 multiples of q
         slmod[j] = LT % e.q;
-        srounds[j] = (LT / e.q + 1 + 31) / 32;  // a tile holds at most floor(L_tile/q)+1 multiples of q
     }
     if (tid == 0) {
         // distinct in-tile primes (their square is an in-tile prime power)
@@ -198,9 +195,10 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
         constexpr int kPer = kMaxSpp / 32;
         // entries (v) and slots (w) of prime power j
         auto counts = [&](uint32_t j, uint32_t &v, uint32_t &w) {
-            const bool single = j < nspp && srounds[j] == 1;
-            v = j < nspp && !single ? (srounds[j] + kRoundsPerEntry - 1) / kRoundsPerEntry : 0;
-            w = single ? LT / sq[j] + 1 : 0;  // at most 32
+            const uint32_t rounds = j < nspp ? sdesc[j].w : 0u;
+            const bool single = rounds == 1;
+            v = rounds > 1 ? (rounds + kRoundsPerEntry - 1) / kRoundsPerEntry : 0;
+            w = single ? LT / sdesc[j].x + 1 : 0;  // at most 32
         };
         uint32_t sum = 0, sumw = 0;
         for (int u = 0; u < kPer; u++) {
@@ -255,9 +253,9 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
         const unsigned long long ncache = P.seg_log2 <= 19 ? (unsigned long long)kLogBucketCache : 0ull;
         const uint32_t nbc = (uint32_t)((b1 - b0) < ncache ? (b1 - b0) : ncache);
         for (uint32_t j = tid; j < nspp; j += NT) {
-            const uint32_t q = sq[j];
+            const uint32_t q = sdesc[j].x;
             const uint32_t r = (uint32_t)(seg_lo % q);
-            soff[j] = r ? q - r : 0;
+            sdesc[j].z = r ? q - r : 0;
         }
         for (uint32_t e = tid; e < nbc; e += NT) bcache[e] = pack_hit(P.bent[b0 + e]);
         const uint32_t nsched = s_nsched, nsparse = s_nsparse;
@@ -293,22 +291,30 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
                     const uint32_t e = sched[g];
                     const uint32_t j = e & 255u;
                     const uint32_t r0 = (e >> 8) * kRoundsPerEntry;
-                    const uint32_t q = sq[j];
-                    const uint32_t reps = min(kRoundsPerEntry, srounds[j] - r0);
-                    uint32_t x = soff[j] + ((r0 << 5) + lane) * q;
-                    // q is odd and 32q even: the parity of x, hence the half-word, is fixed per lane
-                    const uint32_t lg = W16 ? slg[j] << ((x & 1) << 4) : slg[j];
+                    const uint4 d = sdesc[j];
+                    const uint32_t q = d.x;
+                    const uint32_t reps = min(kRoundsPerEntry, d.w - r0);
+                    const uint32_t x = d.z + ((r0 << 5) + lane) * q;
+                    // q is odd and 32q even: the parity of x, hence the half-word, is fixed per lane.
+                    // The lane strikes x, x + 32q, ... up to xl, the last of its multiples in this
+                    // entry and in the tile; in words: up to the word of xl rounded down to x's parity.
+                    const uint32_t xl = min(tl, x + (reps - 1) * 32 * q);
+                    const uint32_t lg = W16 ? d.y << ((x & 1) << 4) : d.y;
+                    uint32_t *a = W16 ? &tile[x >> 1] : &tile[x];
+                    const uint32_t *alim = W16 ? &tile[(xl - ((xl ^ x) & 1)) >> 1] : &tile[xl];
+                    const uint32_t wstep = W16 ? 16 * q : 32 * q;
 #pragma unroll
-                    for (uint32_t r = 0; r < kRoundsPerEntry; r++, x += 32 * q) {
-                        if (r < reps && x <= tl) atomicAdd(W16 ? &tile[x >> 1] : &tile[x], lg);
+                    for (uint32_t r = 0; r < kRoundsPerEntry; r++, a += wstep) {
+                        if (a <= alim) atomicAdd(a, lg);
                     }
                 } else {  // packed slots of the single-round prime powers
                     const uint32_t sl = (g - nsched) * 32 + lane;
                     if (sl < nsparse) {
                         const uint32_t e = sched[nsched + sl];
                         const uint32_t j = e & 255u;
-                        const uint32_t x = soff[j] + (e >> 8) * sq[j];
-                        if (x <= tl) atomicAdd(W16 ? &tile[x >> 1] : &tile[x], W16 ? slg[j] << ((x & 1) << 4) : slg[j]);
+                        const uint4 d = sdesc[j];
+                        const uint32_t x = d.z + (e >> 8) * d.x;
+                        if (x <= tl) atomicAdd(W16 ? &tile[x >> 1] : &tile[x], W16 ? d.y << ((x & 1) << 4) : d.y);
                     }
                 }
             }
@@ -330,48 +336,56 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
             }
             __syncthreads();
             for (uint32_t j = tid; j < nspp; j += NT) {
-                const uint32_t off = soff[j], lm = slmod[j];
-                soff[j] = off >= lm ? off - lm : off + sq[j] - lm;
+                const uint32_t off = sdesc[j].z, lm = slmod[j];
+                sdesc[j].z = off >= lm ? off - lm : off + sdesc[j].x - lm;
             }
-            // epilogue: G consecutive n per thread (4 u32 values, or 8 u16 values, per 16-byte load)
+            // epilogue: G consecutive n per thread (4 u32 values per 16-byte load, or 16 u16 values
+            // per two 16-byte loads)
             constexpr uint32_t M2 = 1u << kHigh2;
-            constexpr uint32_t G = W16 ? 8u : 4u;
+            constexpr uint32_t G = W16 ? 16u : 4u;
             const uint32_t ngroups = (tl + G - 1) / G;
             const uint4 *t4 = reinterpret_cast<const uint4 *>(tile);
             for (uint32_t base = 0; base < ngroups; base += NT) {
                 const uint32_t g = base + tid;
                 uint32_t cm = 0;  // candidates among the group's n (bit u: n = t_lo + G*g + u)
                 if (g < ngroups) {
-                    const uint4 v = t4[g];
-                    const uint32_t w = tile[4 * g + 4];
-                    uint32_t mx;
                     uint32_t ss[G];
                     bool logc;
                     if constexpr (W16) {
+                        const uint4 v = t4[2 * g], v2 = t4[2 * g + 1];
+                        const uint32_t w = tile[8 * g + 8];
                         // packed pair sums: low half L(2k) + L(2k+1), high half L(2k+1) + L(2k+2)
-                        const uint32_t p0 = v.x + __funnelshift_r(v.x, v.y, 16);
-                        const uint32_t p1 = v.y + __funnelshift_r(v.y, v.z, 16);
-                        const uint32_t p2 = v.z + __funnelshift_r(v.z, v.w, 16);
-                        const uint32_t p3 = v.w + __funnelshift_r(v.w, w, 16);
+                        uint32_t pw[8];
+                        pw[0] = v.x + __funnelshift_r(v.x, v.y, 16);
+                        pw[1] = v.y + __funnelshift_r(v.y, v.z, 16);
+                        pw[2] = v.z + __funnelshift_r(v.z, v.w, 16);
+                        pw[3] = v.w + __funnelshift_r(v.w, v2.x, 16);
+                        pw[4] = v2.x + __funnelshift_r(v2.x, v2.y, 16);
+                        pw[5] = v2.y + __funnelshift_r(v2.y, v2.z, 16);
+                        pw[6] = v2.z + __funnelshift_r(v2.z, v2.w, 16);
+                        pw[7] = v2.w + __funnelshift_r(v2.w, w, 16);
                         // a pair sum is below 2^15: adding 2^15 - T to its half-word sets bit 15
                         // exactly when the sum reaches T, and never carries into the other half
                         const uint32_t K = (0x8000u - (T32 < 0x8000u ? T32 : 0x8000u)) * 0x10001u;
-                        logc = (((p0 + K) | (p1 + K) | (p2 + K) | (p3 + K)) & 0x80008000u) != 0u;
-                        ss[0] = p0 & 0xffffu; ss[1] = p0 >> 16; ss[2] = p1 & 0xffffu; ss[3] = p1 >> 16;
-                        ss[4] = p2 & 0xffffu; ss[5] = p2 >> 16; ss[6] = p3 & 0xffffu; ss[7] = p3 >> 16;
-                        mx = 0;
+                        logc = (((pw[0] + K) | (pw[1] + K) | (pw[2] + K) | (pw[3] + K) | (pw[4] + K) | (pw[5] + K) |
+                                 (pw[6] + K) | (pw[7] + K)) & 0x80008000u) != 0u;
+#pragma unroll
+                        for (uint32_t u = 0; u < 8; u++) {
+                            ss[2 * u] = pw[u] & 0xffffu;
+                            ss[2 * u + 1] = pw[u] >> 16;
+                        }
                     } else {
+                        const uint4 v = t4[g];
+                        const uint32_t w = tile[4 * g + 4];
                         ss[0] = v.x + v.y;
                         ss[1] = v.y + v.z;
                         ss[2] = v.z + v.w;
                         ss[3] = v.w + w;
-                        mx = max(max(ss[0], ss[1]), max(ss[2], ss[3]));
-                        logc = mx >= T32;
+                        logc = max(max(ss[0], ss[1]), max(ss[2], ss[3])) >= T32;
                     }
                     const uint32_t n0 = (uint32_t)(t_lo + G * g);  // low 32 bits suffice modulo 2^M
                     // does [n0, n0 + G] hold a multiple of 2^M?
                     const bool hi2 = ((n0 + G) & (M2 - 1)) <= G;
-                    (void)mx;
                     if (all_cand || logc || hi2) {
 #pragma unroll
                         for (uint32_t u = 0; u < G; u++) {
