@@ -105,13 +105,23 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def sieve_traffic(integers: int):
-    """DRAM bytes of one sieve launch, from the committed ncu capture -- or None
-    once the kernel source differs from the one that capture measured."""
+def sieve_traffic(integers: int, tile_kind: int):
+    """DRAM bytes of one sieve launch, from the committed ncu capture of this tile
+    kind -- or None once the kernel source differs from the one that capture measured."""
+    import glob
     import hashlib
 
+    rec = None
+    for f in glob.glob(os.path.join(ROOT, "profiles", "k_sieve_log_*_traffic.json")):
+        try:
+            r = json.load(open(f))
+        except Exception:
+            continue
+        if r.get("tile_kind") == tile_kind:
+            rec = r
+    if rec is None:
+        return None
     try:
-        rec = json.load(open(os.path.join(ROOT, "profiles", "k_sieve_log_u16_traffic.json")))
         src = open(os.path.join(ROOT, rec["source"]), "rb").read()
     except Exception:
         return None
@@ -377,9 +387,10 @@ def run_ours(args):
             "gpu_launches": KERNELS_PER_STEP * args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
                          "frac": achieved / alu_peak,
-                         "traffic": sieve_traffic(integers) if ctx.tune()["tile_kind"] == 2 else None,
+                         "traffic": sieve_traffic(integers, ctx.tune()["tile_kind"]),
                          "kernel": {0: "k_sieve_log<search, u32 tile>", 1: "k_sieve<search, exact u64 tile>",
-                                    2: "k_sieve_log<search, u16 tile>"}[ctx.tune()["tile_kind"]]
+                                    2: "k_sieve_log<search, u16 tile>",
+                                    3: "k_sieve_log<search, u8 tile>"}[ctx.tune()["tile_kind"]]
                                    + " (persistent shared-memory tile sieve, fused filter + warp-ballot compaction)",
                          "peak_source": "152 SMs x 128 lanes/clk x max SM clock (issue roofline)",
                          "alg_ops_per_integer": ALG_OPS_PER_INT, "sieve_ms_per_launch": ms_sieve,

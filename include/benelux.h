@@ -72,14 +72,15 @@ typedef struct {
 
 /* Tunable launch parameters (all optional in the JSON given to bnx_create). */
 typedef struct {
-    uint32_t tile_log2;    /* shared-memory tile: 2^tile_log2 integers (12..14) */
+    uint32_t tile_log2;    /* shared-memory tile: 2^tile_log2 integers (10..16; the exact
+                              tile uses at most 2^14 and walks a longer one in pieces) */
     uint32_t seg_tiles;    /* tiles per queue segment (1..64) */
     uint32_t threads;      /* threads per CTA (256, 512 or 1024) */
     uint32_t ctas_per_sm;  /* resident CTAs per SM for the persistent grid (0 = occupancy limit) */
     uint32_t small_q_log2; /* prime powers q <= 2^small_q_log2 are struck in shared
                               memory, larger ones come from the HBM buckets (8..16) */
-    uint32_t tile_kind;    /* searches: 0 = log-domain u32 tile, 2 = log-domain u16 tile
-                              (both with exact re-check of candidates), 1 = exact u64
+    uint32_t tile_kind;    /* searches: log-domain tile of 0 = u32, 2 = u16 or 3 = u8 values
+                              (each with exact re-check of candidates), 1 = exact u64
                               square-part tile */
 } bnx_tune;
 

@@ -80,7 +80,7 @@ struct bnx_ctx {
     bool capturing = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_s0 = nullptr, ev_s1 = nullptr;
 
-    bnx::SieveCfg sieve_cfg[9];  // per (mode, tile kind)
+    bnx::SieveCfg sieve_cfg[12];  // per (mode, tile: exact, log u32, log u16, log u8)
     bnx_stats stats{};
     std::mutex mu;
     bnx::Server *server = nullptr;

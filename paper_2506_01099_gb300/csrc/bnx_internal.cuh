@@ -121,7 +121,7 @@ struct Plan {
 
 enum SieveMode { kModeSearch = 0, kModeRad = 1, kModeHash = 2 };
 // which tile the search and hash modes use
-enum TileKind { kTileLog32 = 0, kTileExact = 1, kTileLog16 = 2 };
+enum TileKind { kTileLog32 = 0, kTileExact = 1, kTileLog16 = 2, kTileLog8 = 3 };
 
 // ---------------------------------------------------------------- kernels --
 // tables.cu
@@ -144,9 +144,10 @@ void launch_bucket(const Plan &P, bool fill, int grid, cudaStream_t s);
 void launch_sieve(const Plan &P, int mode, int grid, int threads, size_t smem, cudaStream_t s);
 int sieve_occupancy(int mode, int threads, size_t smem, int *ctas_per_sm);
 // sieve_log.cu: log-domain tile for the search and hash modes
-void launch_sieve_log(const Plan &P, int mode, bool w16, int grid, int threads, size_t smem, cudaStream_t s);
-int sieve_log_occupancy(int mode, int threads, bool w16, size_t smem, int *ctas_per_sm);
-size_t sieve_log_smem_bytes(uint32_t tile_log2, uint32_t nspp, uint32_t nsched, bool w16);
+// vb: bytes per tile value (4, 2 or 1)
+void launch_sieve_log(const Plan &P, int mode, int vb, int grid, int threads, size_t smem, cudaStream_t s);
+int sieve_log_occupancy(int mode, int threads, int vb, size_t smem, int *ctas_per_sm);
+size_t sieve_log_smem_bytes(uint32_t tile_log2, uint32_t nspp, uint32_t nsched, int vb);
 size_t sieve_smem_bytes(uint32_t tile_log2, uint32_t nspp, uint32_t nsched);
 uint32_t sched_length(uint32_t tile_log2, const uint32_t *q, uint32_t nspp);
 

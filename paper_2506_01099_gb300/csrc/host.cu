@@ -60,17 +60,17 @@ static void tune_defaults(bnx_tune *t) {
     t->threads = 256;
     t->ctas_per_sm = 0;
     t->small_q_log2 = 14;
-    t->tile_kind = kTileLog16;
+    t->tile_kind = kTileLog8;
 }
 
 static int tune_check(const bnx_tune *t) {
-    if (t->tile_log2 < 10 || t->tile_log2 > 15) return fail(BNX_E_ARG, "tile_log2 must be in [10, 15]");
+    if (t->tile_log2 < 10 || t->tile_log2 > 16) return fail(BNX_E_ARG, "tile_log2 must be in [10, 16]");
     if (t->seg_tiles < 1 || t->seg_tiles > 64 || (t->seg_tiles & (t->seg_tiles - 1)))
         return fail(BNX_E_ARG, "seg_tiles must be a power of two in [1, 64]");
     if (t->threads != 128 && t->threads != 256 && t->threads != 512 && t->threads != 1024)
         return fail(BNX_E_ARG, "threads must be 128, 256, 512 or 1024");
     if (t->small_q_log2 < 8 || t->small_q_log2 > 16) return fail(BNX_E_ARG, "small_q_log2 must be in [8, 16]");
-    if (t->tile_kind > 2) return fail(BNX_E_ARG, "tile_kind must be 0, 1 or 2");
+    if (t->tile_kind > 3) return fail(BNX_E_ARG, "tile_kind must be 0, 1, 2 or 3");
     if (t->ctas_per_sm > 32) return fail(BNX_E_ARG, "ctas_per_sm must be <= 32");
     return BNX_OK;
 }
@@ -293,14 +293,18 @@ static bool use_log_tile(const bnx_ctx *c, int mode) { return mode != kModeRad &
 static uint32_t tile_log2_for(const bnx_ctx *c, int mode) {
     return use_log_tile(c, mode) ? c->tune.tile_log2 : std::min<uint32_t>(c->tune.tile_log2, 14u);
 }
-static bool use_w16(const bnx_ctx *c) { return c->tune.tile_kind == kTileLog16; }
+// bytes per value of the log-domain tile
+static int log_vb(const bnx_ctx *c) {
+    return c->tune.tile_kind == kTileLog8 ? 1 : c->tune.tile_kind == kTileLog16 ? 2 : 4;
+}
 
 int sieve_config(bnx_ctx *c, int mode, int *grid, int *threads, size_t *smem) {
-    const bool lg = use_log_tile(c, mode), w16 = lg && use_w16(c);
-    SieveCfg &sc = c->sieve_cfg[mode * 3 + (lg ? (w16 ? 2 : 1) : 0)];
+    const bool lg = use_log_tile(c, mode);
+    const int vb = lg ? log_vb(c) : 8;
+    SieveCfg &sc = c->sieve_cfg[mode * 4 + (lg ? (vb == 4 ? 1 : vb == 2 ? 2 : 3) : 0)];
     const uint32_t tlog = tile_log2_for(c, mode);
     const uint32_t nsched = sched_length(tlog, c->h_spp_q.data(), c->n_spp);
-    const size_t want_smem = lg ? sieve_log_smem_bytes(tlog, c->n_spp, nsched, w16)
+    const size_t want_smem = lg ? sieve_log_smem_bytes(tlog, c->n_spp, nsched, vb)
                                 : sieve_smem_bytes(tlog, c->n_spp, nsched);
     if (!sc.valid || sc.tile_log2 != tlog || sc.threads != c->tune.threads ||
         sc.ctas != c->tune.ctas_per_sm || sc.smem != want_smem) {
@@ -308,7 +312,7 @@ int sieve_config(bnx_ctx *c, int mode, int *grid, int *threads, size_t *smem) {
         const int thr = (int)c->tune.threads;
         const size_t smem_b = want_smem;
         int occ = 0;
-        int e = lg ? sieve_log_occupancy(mode, thr, w16, smem_b, &occ) : sieve_occupancy(mode, thr, smem_b, &occ);
+        int e = lg ? sieve_log_occupancy(mode, thr, vb, smem_b, &occ) : sieve_occupancy(mode, thr, smem_b, &occ);
         if (e != 0) return fail(BNX_E_CUDA, "sieve occupancy query failed: %s", cudaGetErrorString((cudaError_t)e));
         if (occ < 1) return fail(BNX_E_ARG, "sieve kernel does not fit an SM with this tuning");
         const int per = c->tune.ctas_per_sm ? std::min<int>((int)c->tune.ctas_per_sm, occ) : occ;
@@ -345,7 +349,7 @@ int record_pipeline(bnx_ctx *c, int mode, cudaStream_t s, bool timing) {
     CUDA_TRY(cudaMemsetAsync(c->bcnt.p, 0, c->bcnt.bytes, s));
     launch_bucket(P, true, bgrid, s);
     if (timing) CUDA_TRY(cudaEventRecordWithFlags(c->ev_s0, s, c->capturing ? cudaEventRecordExternal : 0));
-    if (use_log_tile(c, mode)) launch_sieve_log(P, mode, use_w16(c), sgrid, sthreads, ssmem, s);
+    if (use_log_tile(c, mode)) launch_sieve_log(P, mode, log_vb(c), sgrid, sthreads, ssmem, s);
     else launch_sieve(P, mode, sgrid, sthreads, ssmem, s);
     if (timing) CUDA_TRY(cudaEventRecordWithFlags(c->ev_s1, s, c->capturing ? cudaEventRecordExternal : 0));
     if (mode == kModeSearch) {

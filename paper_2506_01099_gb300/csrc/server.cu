@@ -253,23 +253,23 @@ int bnx_autotune(bnx_ctx *c, const bnx_interval *iv, size_t k, int rounds, char 
     float best_ms = 0;
     int rc = time_of(best, &best_ms);
     if (rc) return rc;
-    const uint32_t tiles[] = {13, 14, 15};
+    const uint32_t tiles[] = {13, 14, 15, 16};
     const uint32_t segt[] = {2, 4, 8, 16, 32};
     const uint32_t thr[] = {128, 256, 512, 1024};
     const uint32_t qs[] = {12, 13, 14, 15, 16};
     const uint32_t ctas[] = {0, 1, 2};
-    const uint32_t kinds[] = {0, 2};
+    const uint32_t kinds[] = {0, 2, 3};
     for (int pass = 0; pass < 2; pass++) {
         for (int field = 0; field < 6; field++) {
             const uint32_t *vals;
             int nv;
             switch (field) {
-                case 0: vals = tiles; nv = 3; break;
+                case 0: vals = tiles; nv = 4; break;
                 case 1: vals = segt; nv = 5; break;
                 case 2: vals = thr; nv = 4; break;
                 case 3: vals = qs; nv = 5; break;
                 case 4: vals = ctas; nv = 3; break;
-                default: vals = kinds; nv = 2; break;
+                default: vals = kinds; nv = 3; break;
             }
             for (int v = 0; v < nv; v++) {
                 bnx_tune t = best;

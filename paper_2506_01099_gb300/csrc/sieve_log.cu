@@ -1,8 +1,9 @@
 // Log-domain tile sieve for the search and hash modes (the default).
 //
 // The tile holds, per value x, L(x) = the sum of lg(p) over the prime-power
-// strikes at x, where lg(p) = floor(2^16 log2 p) + 1 > 2^16 log2 p.  So L(x) is
-// an upper bound of 2^16 log2 s_odd(x), s_odd(x) being the odd part of
+// strikes at x, where lg(p) = floor(F log2 p) + 1 > F log2 p in the tile's
+// fixed-point scale F (2^16 for u32 values, 2^8 for u16, 2 for u8).  So L(x) is
+// an upper bound of F log2 s_odd(x), s_odd(x) being the odd part of
 // x / rad(x).  Strikes are 32-bit shared-memory reductions (no read-modify-write
 // loop: addition commutes, so strikes of different prime powers at one x need
 // no ordering).  Algorithm 1 (Sec. 2.1) still decides which x a prime power
@@ -12,7 +13,7 @@
 // conditions need 2P >= n+1 (second kind, and a fortiori the first) or
 // P >= n(n+1)/(2S) (hash search).  If neither n nor n+1 is divisible by 2^M
 // (M = 16), the power of 2 in P is at most 2^(M-2), so
-//   log2 P <= (L(n) + L(n+1)) / 2^16 + M - 2,
+//   log2 P <= (L(n) + L(n+1)) / F + M - 2,
 // and n is rejected when that bound falls below the tile's smallest threshold.
 // Every other n (a bound that does not reject, or n, n+1 next to a multiple of
 // 2^M) is a candidate.  A candidate whose exact power of 2 still rejects it is
@@ -30,8 +31,9 @@ namespace {
 // margin (p < 2^22: lg7 < 2^12).  Offsets reach the segment length, so the
 // cache is used for segments of at most 2^19 values; larger segments read all
 // their entries from global memory.  A strike
-// adds lg7 << 1 to the u16 tile (units 2^-8) or lg7 << 9 to the u32 tile
-// (units 2^-16): an over-estimate of log2 p, as the rejection rule needs.
+// adds lg7 << 9 to the u32 tile (units 2^-16), lg7 << 1 to the u16 tile (units
+// 2^-8) or ceil(lg7 / 2^6) to the u8 tile (units 2^-1): an over-estimate of
+// log2 p, as the rejection rule needs.
 constexpr int kLogBucketCache = 1024;
 constexpr uint32_t kHigh2 = 16;
 constexpr int kMaxSmallPrimes = 64;
@@ -58,12 +60,12 @@ struct LogLayout {
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-// Tile words: one u32 per value, or (w16) two u16 values per u32 word; the
-// slack covers the epilogue's read past the last value.
-__host__ __device__ inline LogLayout log_layout(uint32_t tile_log2, uint32_t nspp, uint32_t nsched, bool w16) {
+// Tile words: one u32 value per word, or two u16 or four u8 values per word
+// (vb = bytes per value); the slack covers the epilogue's read past the last value.
+__host__ __device__ inline LogLayout log_layout(uint32_t tile_log2, uint32_t nspp, uint32_t nsched, int vb) {
     LogLayout L;
     L.tile = 0;
-    const size_t words = w16 ? ((size_t)1 << tile_log2) / 2 + 8 : ((size_t)1 << tile_log2) + 8;
+    const size_t words = ((size_t)1 << tile_log2) * vb / 4 + 8;
     L.spp = al16(words * sizeof(uint32_t));
     L.sched = L.spp + al16((size_t)5 * (nspp ? nspp : 1) * sizeof(uint32_t));
     L.bcache = L.sched + al16((size_t)(nsched ? nsched : 1) * sizeof(uint16_t));
@@ -136,17 +138,29 @@ struct LogMinBlocks {  // 64 registers per thread at every CTA size
     static constexpr int value = NT <= 128 ? 8 : NT <= 256 ? 4 : NT <= 512 ? 2 : 1;
 };
 
-// W16: the tile keeps L(x) in 16 bits with 8 fractional bits (two values per
-// 32-bit word; a sum stays below 42*2^8 + 42 < 2^15, so a strike's addition of
-// lg << 16*(x&1) never carries into the neighbour, and a pair sum stays below 2^16).
-template <int MODE, int NT, bool W16>
+// VB = bytes per tile value.
+//  VB = 4: L(x) in 32 bits with 16 fractional bits.
+//  VB = 2: 16 bits with 8 fractional bits, two values per 32-bit word.  For x < 2^42
+//    L(x) <= 2^8 log2 s_odd(x) + (strikes at x) < 42 * 2^8 + 42 < 2^14, and a pair sum
+//    L(n) + L(n+1) < 2^15, so a strike's addition of lg << 16*(x&1) never carries into
+//    the neighbour, nor does a pair sum.
+//  VB = 1: 8 bits with 1 fractional bit (half-bit units), four values per word.  lg(p)
+//    = floor(2 log2 p) + 1 is at most 4/log2(3) = 2.52 units per bit of p (p = 3 is the
+//    worst; a bucket prime p > 2^7 takes at most 2 + 2/7 units per bit), so for x < 2^42
+//    L(x) <= 2.52 * 41 < 2^7 and a pair sum L(n) + L(n+1) <= 2.52 * 84 < 2^8: neither a
+//    strike nor a pair sum carries into the neighbouring byte.
+template <int MODE, int NT, int VB>
 __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr uint32_t FS = W16 ? 256u : 65536u;  // fixed-point scale of L
+    constexpr uint32_t FS = VB == 4 ? 65536u : VB == 2 ? 256u : 2u;  // fixed-point scale of L
+    constexpr uint32_t VSH = VB == 4 ? 0u : VB == 2 ? 1u : 2u;       // value index >> VSH = word index
+    constexpr uint32_t VPW = 1u << VSH;                             // values per word
+    constexpr uint32_t VBITS = 8u * VB;
+    constexpr uint32_t VMASK = VB == 4 ? 0xffffffffu : (1u << VBITS) - 1u;
     const uint32_t tile_log2 = P.tile_log2;
     const uint32_t LT = 1u << tile_log2;
     const uint32_t nspp = P.n_spp;
-    const LogLayout lay = log_layout(tile_log2, nspp, P.n_sched, W16);
+    const LogLayout lay = log_layout(tile_log2, nspp, P.n_sched, VB);
     uint32_t *tile = reinterpret_cast<uint32_t *>(smem_raw + lay.tile);
     // per in-tile prime power j: {q, lg, offset of its first multiple in the tile, 32-multiple rounds per tile}
     uint4 *sdesc = reinterpret_cast<uint4 *>(smem_raw + lay.spp);
@@ -165,8 +179,8 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
 
     for (uint32_t j = tid; j < nspp; j += NT) {
         const SmallPP e = P.spp[j];
-        sdesc[j] = make_uint4(e.q, W16 ? (uint32_t)floor(log2((double)e.p) * 256.0) + 1u : e.lg, 0u,
-                              (LT / e.q + 1 + 31) / 32);  // a tile holds at most floor(L_tile/q)+1 multiples of q
+        const uint32_t lg = VB == 4 ? e.lg : (uint32_t)floor(log2((double)e.p) * (double)FS) + 1u;
+        sdesc[j] = make_uint4(e.q, lg, 0u, (LT / e.q + 1 + 31) / 32);  // at most floor(L_tile/q)+1 multiples of q
         slmod[j] = LT % e.q;
     }
     if (tid == 0) {
@@ -282,7 +296,9 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
             {
                 uint4 *t4 = reinterpret_cast<uint4 *>(tile);
                 const uint4 z = make_uint4(0, 0, 0, 0);
-                const uint32_t n4 = W16 ? ((tl >> 1) + 8 + 3) >> 2 : ((tl + 4) >> 2) + 1;
+                // values [0, tl] and the slack after them (the epilogue's reads past tl see only
+                // zeros or values of earlier tiles; either only adds candidates, which are masked)
+                const uint32_t n4 = VB == 4 ? ((tl + 4) >> 2) + 1 : ((tl >> VSH) + 8 + 3) >> 2;
                 for (uint32_t i = tid; i < n4; i += NT) t4[i] = z;
             }
             __syncthreads();
@@ -295,17 +311,21 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
                     const uint32_t q = d.x;
                     const uint32_t reps = min(kRoundsPerEntry, d.w - r0);
                     const uint32_t x = d.z + ((r0 << 5) + lane) * q;
-                    // q is odd and 32q even: the parity of x, hence the half-word, is fixed per lane.
-                    // The lane strikes x, x + 32q, ... up to xl, the last of its multiples in this
-                    // entry and in the tile; in words: up to the word of xl rounded down to x's parity.
+                    // 32q is a multiple of 4: x mod 4, hence the value's place in its word, is fixed
+                    // per lane.  The lane strikes x, x + 32q, ... up to xl, the last of its multiples
+                    // in this entry and in the tile; in words: up to the word of the largest value
+                    // <= xl congruent to x mod VPW.  For VPW <= 2 that bound cannot wrap (xl = 0
+                    // only when x = 0); for VPW = 4 the lanes with x > xl skip the entry.
                     const uint32_t xl = min(tl, x + (reps - 1) * 32 * q);
-                    const uint32_t lg = W16 ? d.y << ((x & 1) << 4) : d.y;
-                    uint32_t *a = W16 ? &tile[x >> 1] : &tile[x];
-                    const uint32_t *alim = W16 ? &tile[(xl - ((xl ^ x) & 1)) >> 1] : &tile[xl];
-                    const uint32_t wstep = W16 ? 16 * q : 32 * q;
+                    if (VPW < 4 || x <= xl) {
+                        const uint32_t lg = d.y << ((x & (VPW - 1)) * VBITS);
+                        uint32_t *a = &tile[x >> VSH];
+                        const uint32_t *alim = &tile[(xl - ((xl - x) & (VPW - 1))) >> VSH];
+                        const uint32_t wstep = (32 >> VSH) * q;
 #pragma unroll
-                    for (uint32_t r = 0; r < kRoundsPerEntry; r++, a += wstep) {
-                        if (a <= alim) atomicAdd(a, lg);
+                        for (uint32_t r = 0; r < kRoundsPerEntry; r++, a += wstep) {
+                            if (a <= alim) atomicAdd(a, lg);
+                        }
                     }
                 } else {  // packed slots of the single-round prime powers
                     const uint32_t sl = (g - nsched) * 32 + lane;
@@ -314,7 +334,7 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
                         const uint32_t j = e & 255u;
                         const uint4 d = sdesc[j];
                         const uint32_t x = d.z + (e >> 8) * d.x;
-                        if (x <= tl) atomicAdd(W16 ? &tile[x >> 1] : &tile[x], W16 ? d.y << ((x & 1) << 4) : d.y);
+                        if (x <= tl) atomicAdd(&tile[x >> VSH], d.y << ((x & (VPW - 1)) * VBITS));
                     }
                 }
             }
@@ -322,16 +342,17 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
                 const uint32_t w = bcache[e];
                 const uint32_t x = (w >> 12) - t0;  // wraps to a large value below t0
                 if (x <= tl) {
-                    if (W16) atomicAdd(&tile[x >> 1], (w & 0xfffu) << (1 + ((x & 1) << 4)));
-                    else atomicAdd(&tile[x], (w & 0xfffu) << 9);
+                    const uint32_t lg7 = w & 0xfffu;
+                    const uint32_t lg = VB == 4 ? lg7 << 9 : VB == 2 ? lg7 << 1 : (lg7 + 63u) >> 6;
+                    atomicAdd(&tile[x >> VSH], lg << ((x & (VPW - 1)) * VBITS));
                 }
             }
             for (unsigned long long e = b0 + nbc + tid; e < b1; e += NT) {
                 const uint2 h = P.bent[e];
                 if (h.x >= t0 && h.x <= t0 + tl) {
                     const uint32_t x = h.x - t0;
-                    if (W16) atomicAdd(&tile[x >> 1], lg_large8(h.y) << ((x & 1) << 4));
-                    else atomicAdd(&tile[x], lg_large(h.y));
+                    const uint32_t lg = VB == 4 ? lg_large(h.y) : VB == 2 ? lg_large8(h.y) : (lg_large8(h.y) + 127u) >> 7;
+                    atomicAdd(&tile[x >> VSH], lg << ((x & (VPW - 1)) * VBITS));
                 }
             }
             __syncthreads();
@@ -339,10 +360,10 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
                 const uint32_t off = sdesc[j].z, lm = slmod[j];
                 sdesc[j].z = off >= lm ? off - lm : off + sdesc[j].x - lm;
             }
-            // epilogue: G consecutive n per thread (4 u32 values per 16-byte load, or 16 u16 values
-            // per two 16-byte loads)
+            // epilogue: G consecutive n per thread (4 u32 values per 16-byte load; 16 u16 or 32 u8
+            // values per two 16-byte loads)
             constexpr uint32_t M2 = 1u << kHigh2;
-            constexpr uint32_t G = W16 ? 16u : 4u;
+            constexpr uint32_t G = VB == 4 ? 4u : VB == 2 ? 16u : 32u;
             const uint32_t ngroups = (tl + G - 1) / G;
             const uint4 *t4 = reinterpret_cast<const uint4 *>(tile);
             for (uint32_t base = 0; base < ngroups; base += NT) {
@@ -351,30 +372,7 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
                 if (g < ngroups) {
                     uint32_t ss[G];
                     bool logc;
-                    if constexpr (W16) {
-                        const uint4 v = t4[2 * g], v2 = t4[2 * g + 1];
-                        const uint32_t w = tile[8 * g + 8];
-                        // packed pair sums: low half L(2k) + L(2k+1), high half L(2k+1) + L(2k+2)
-                        uint32_t pw[8];
-                        pw[0] = v.x + __funnelshift_r(v.x, v.y, 16);
-                        pw[1] = v.y + __funnelshift_r(v.y, v.z, 16);
-                        pw[2] = v.z + __funnelshift_r(v.z, v.w, 16);
-                        pw[3] = v.w + __funnelshift_r(v.w, v2.x, 16);
-                        pw[4] = v2.x + __funnelshift_r(v2.x, v2.y, 16);
-                        pw[5] = v2.y + __funnelshift_r(v2.y, v2.z, 16);
-                        pw[6] = v2.z + __funnelshift_r(v2.z, v2.w, 16);
-                        pw[7] = v2.w + __funnelshift_r(v2.w, w, 16);
-                        // a pair sum is below 2^15: adding 2^15 - T to its half-word sets bit 15
-                        // exactly when the sum reaches T, and never carries into the other half
-                        const uint32_t K = (0x8000u - (T32 < 0x8000u ? T32 : 0x8000u)) * 0x10001u;
-                        logc = (((pw[0] + K) | (pw[1] + K) | (pw[2] + K) | (pw[3] + K) | (pw[4] + K) | (pw[5] + K) |
-                                 (pw[6] + K) | (pw[7] + K)) & 0x80008000u) != 0u;
-#pragma unroll
-                        for (uint32_t u = 0; u < 8; u++) {
-                            ss[2 * u] = pw[u] & 0xffffu;
-                            ss[2 * u + 1] = pw[u] >> 16;
-                        }
-                    } else {
+                    if constexpr (VB == 4) {
                         const uint4 v = t4[g];
                         const uint32_t w = tile[4 * g + 4];
                         ss[0] = v.x + v.y;
@@ -382,6 +380,41 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
                         ss[2] = v.z + v.w;
                         ss[3] = v.w + w;
                         logc = max(max(ss[0], ss[1]), max(ss[2], ss[3])) >= T32;
+                    } else {
+                        const uint4 v = t4[2 * g], v2 = t4[2 * g + 1];
+                        const uint32_t w = tile[8 * g + 8];
+                        // packed pair sums: field i of pw[k] is L(VPW k + i) + L(VPW k + i + 1)
+                        uint32_t pw[8];
+                        pw[0] = v.x + __funnelshift_r(v.x, v.y, VBITS);
+                        pw[1] = v.y + __funnelshift_r(v.y, v.z, VBITS);
+                        pw[2] = v.z + __funnelshift_r(v.z, v.w, VBITS);
+                        pw[3] = v.w + __funnelshift_r(v.w, v2.x, VBITS);
+                        pw[4] = v2.x + __funnelshift_r(v2.x, v2.y, VBITS);
+                        pw[5] = v2.y + __funnelshift_r(v2.y, v2.z, VBITS);
+                        pw[6] = v2.z + __funnelshift_r(v2.z, v2.w, VBITS);
+                        pw[7] = v2.w + __funnelshift_r(v2.w, w, VBITS);
+                        if constexpr (VB == 2) {
+                            // a pair sum is below 2^15: adding 2^15 - T to its half-word sets bit 15
+                            // exactly when the sum reaches T, and never carries into the other half
+                            const uint32_t K = (0x8000u - (T32 < 0x8000u ? T32 : 0x8000u)) * 0x10001u;
+                            logc = (((pw[0] + K) | (pw[1] + K) | (pw[2] + K) | (pw[3] + K) | (pw[4] + K) |
+                                     (pw[5] + K) | (pw[6] + K) | (pw[7] + K)) & 0x80008000u) != 0u;
+                        } else {
+                            // a byte pair sum s is below 2^8.  With T' = min(T, 127) and K = 128 - T',
+                            // s >= T' sets bit 7 of s + K (plus a carry from the byte below), unless
+                            // that sum reaches 2^8 -- and then s >= 128 + T' - 1 has bit 7 set itself.
+                            // So bit 7 of s | (s + K) is set whenever s >= T; carries between bytes
+                            // only add flags, and flagged values are re-checked one by one below.
+                            const uint32_t K = (0x80u - (T32 < 0x7fu ? T32 : 0x7fu)) * 0x01010101u;
+                            uint32_t acc = 0;
+#pragma unroll
+                            for (uint32_t u = 0; u < 8; u++) acc |= pw[u] | (pw[u] + K);
+                            logc = (acc & 0x80808080u) != 0u;
+                        }
+#pragma unroll
+                        for (uint32_t u = 0; u < 8; u++)
+#pragma unroll
+                            for (uint32_t b = 0; b < VPW; b++) ss[VPW * u + b] = (pw[u] >> (b * VBITS)) & VMASK;
                     }
                     const uint32_t n0 = (uint32_t)(t_lo + G * g);  // low 32 bits suffice modulo 2^M
                     // does [n0, n0 + G] hold a multiple of 2^M?
@@ -404,8 +437,8 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
                         const uint32_t i = G * g + u;
                         n = t_lo + i;
                         const uint32_t e2 = ctz64(n + (n & 1)) - 1;  // power of 2 in P
-                        const uint32_t L0 = W16 ? (tile[i >> 1] >> ((i & 1) << 4)) & 0xffffu : tile[i];
-                        const uint32_t L1 = W16 ? (tile[(i + 1) >> 1] >> (((i + 1) & 1) << 4)) & 0xffffu : tile[i + 1];
+                        const uint32_t L0 = (tile[i >> VSH] >> ((i & (VPW - 1)) * VBITS)) & VMASK;
+                        const uint32_t L1 = (tile[(i + 1) >> VSH] >> (((i + 1) & (VPW - 1)) * VBITS)) & VMASK;
                         const int64_t ub = (int64_t)(L0 + L1) + (int64_t)e2 * FS;
                         int need;  // log2 P <= ub / FS must reach it
                         if (MODE == kModeSearch) {
@@ -451,37 +484,41 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT>::value) k_sieve_log(Plan 
     }
 }
 
-template <int MODE, bool W16>
+template <int MODE, int VB>
 const void *log_fn_t(int threads) {
     switch (threads) {
-        case 128: return (const void *)k_sieve_log<MODE, 128, W16>;
-        case 256: return (const void *)k_sieve_log<MODE, 256, W16>;
-        case 512: return (const void *)k_sieve_log<MODE, 512, W16>;
-        default: return (const void *)k_sieve_log<MODE, 1024, W16>;
+        case 128: return (const void *)k_sieve_log<MODE, 128, VB>;
+        case 256: return (const void *)k_sieve_log<MODE, 256, VB>;
+        case 512: return (const void *)k_sieve_log<MODE, 512, VB>;
+        default: return (const void *)k_sieve_log<MODE, 1024, VB>;
     }
 }
 
-const void *log_fn(int mode, int threads, bool w16) {
-    if (w16) return mode == kModeHash ? log_fn_t<kModeHash, true>(threads) : log_fn_t<kModeSearch, true>(threads);
-    return mode == kModeHash ? log_fn_t<kModeHash, false>(threads) : log_fn_t<kModeSearch, false>(threads);
+template <int MODE>
+const void *log_fn_m(int threads, int vb) {
+    return vb == 1 ? log_fn_t<MODE, 1>(threads) : vb == 2 ? log_fn_t<MODE, 2>(threads) : log_fn_t<MODE, 4>(threads);
+}
+
+const void *log_fn(int mode, int threads, int vb) {
+    return mode == kModeHash ? log_fn_m<kModeHash>(threads, vb) : log_fn_m<kModeSearch>(threads, vb);
 }
 
 }  // namespace
 
-size_t sieve_log_smem_bytes(uint32_t tile_log2, uint32_t nspp, uint32_t nsched, bool w16) {
-    return log_layout(tile_log2, nspp, nsched, w16).total;
+size_t sieve_log_smem_bytes(uint32_t tile_log2, uint32_t nspp, uint32_t nsched, int vb) {
+    return log_layout(tile_log2, nspp, nsched, vb).total;
 }
 
-int sieve_log_occupancy(int mode, int threads, bool w16, size_t smem, int *ctas_per_sm) {
-    const void *fn = log_fn(mode, threads, w16);
+int sieve_log_occupancy(int mode, int threads, int vb, size_t smem, int *ctas_per_sm) {
+    const void *fn = log_fn(mode, threads, vb);
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, fn, threads, smem);
 }
 
-void launch_sieve_log(const Plan &P, int mode, bool w16, int grid, int threads, size_t smem, cudaStream_t s) {
+void launch_sieve_log(const Plan &P, int mode, int vb, int grid, int threads, size_t smem, cudaStream_t s) {
     void *args[] = {(void *)&P};
-    cudaLaunchKernel(log_fn(mode, threads, w16), dim3(grid), dim3(threads), args, smem, s);
+    cudaLaunchKernel(log_fn(mode, threads, vb), dim3(grid), dim3(threads), args, smem, s);
 }
 
 }  // namespace bnx

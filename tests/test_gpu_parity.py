@@ -92,7 +92,13 @@ def test_rad_segment_large_sampled(ctx, orc):
                                   dict(tile_kind=2, tile_log2=15, seg_tiles=16, small_q_log2=8),
                                   # 2^20-value segments: the cache is off, every entry read from HBM
                                   dict(tile_kind=2, tile_log2=15, seg_tiles=32),
-                                  dict(tile_kind=0, tile_log2=14, seg_tiles=64, small_q_log2=9)])
+                                  dict(tile_kind=0, tile_log2=14, seg_tiles=64, small_q_log2=9),
+                                  dict(tile_kind=3),
+                                  dict(tile_kind=3, tile_log2=13, threads=128, small_q_log2=16),
+                                  dict(tile_kind=3, tile_log2=16, seg_tiles=2, threads=512),
+                                  dict(tile_kind=3, tile_log2=12, seg_tiles=8, threads=1024, small_q_log2=8),
+                                  dict(tile_kind=3, tile_log2=15, seg_tiles=32),
+                                  dict(tile_kind=2, tile_log2=16, seg_tiles=4)])
 def test_tunings_agree(B, orc, tune):
     with B.Context(0, max_hi=1 << 41) as c:
         c.set_tune(**tune)
@@ -132,6 +138,20 @@ def test_filter_counts_high_window(ctx, orc):
     assert got == orc.pairs_crt(lo, hi)
     st = ctx.stats()
     assert (st["survivors1"], st["survivors2"]) == orc.filter_counts(lo, hi)
+
+
+@pytest.mark.parametrize("tile_kind", [0, 2, 3])
+def test_log_tiles_at_large_square_parts(B, orc, tile_kind):
+    """Windows around the n below 2^42 with the largest odd square parts (3^26, 5^17, 7^14,
+    2 * 3^25), where the log-domain tile values and pair sums are largest: pairs and
+    survivor counts equal the oracle's for every tile width."""
+    with B.Context(0, max_hi=1 << 42) as c:
+        c.set_tune(tile_kind=tile_kind)
+        for center in (3**26, 5**17, 7**14, 2 * 3**25):
+            lo, hi = center - 12_000, center + 12_000
+            assert c.search(lo, hi) == orc.pairs_crt(lo, hi), center
+            st = c.stats()
+            assert (st["survivors1"], st["survivors2"]) == orc.filter_counts(lo, hi), center
 
 
 def test_search_edges(ctx, orc):
