@@ -59,7 +59,7 @@ static void tune_defaults(bnx_tune *t) {
     t->seg_tiles = 8;
     t->threads = 256;
     t->ctas_per_sm = 0;
-    t->small_q_log2 = 14;
+    t->small_q_log2 = 15;
     t->tile_kind = kTileLog8;
 }
 
