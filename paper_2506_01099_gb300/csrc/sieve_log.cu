@@ -37,7 +37,15 @@ namespace {
 constexpr int kLogBucketCache = 1024;
 constexpr uint32_t kHigh2 = 16;
 constexpr int kMaxSmallPrimes = 64;
-constexpr uint32_t kRoundsPerEntry = 4;  // a schedule entry strikes up to 4 x 32 multiples of one q
+// Runs of dense strike rounds per warp (a warp's equal share of all dense rounds of a tile
+// touches at most every dense prime power once; for tiles up to 2^16 there are at most 21:
+// odd p^k <= 2^16/31 with k >= 2)
+constexpr uint32_t kMaxRuns = 24;
+
+// shared-memory reduction (no return value) at a 32-bit shared-window address
+__device__ __forceinline__ void red_add_shared(uint32_t addr, uint32_t v) {
+    asm volatile("red.shared.add.u32 [%0], %1;" ::"r"(addr), "r"(v) : "memory");
+}
 
 __device__ __forceinline__ uint32_t ctz64(uint64_t x) { return (uint32_t)(__ffsll((long long)x) - 1); }
 __device__ __forceinline__ uint32_t flog2_64(uint64_t x) { return 63u - (uint32_t)__clzll((long long)x); }
@@ -170,9 +178,13 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
     uint32_t *slmod = reinterpret_cast<uint32_t *>(sdesc + nspp);  // L_tile mod q
     uint16_t *sched = reinterpret_cast<uint16_t *>(smem_raw + lay.sched);
     uint32_t *bcache = reinterpret_cast<uint32_t *>(smem_raw + lay.bcache);
+    const uint32_t tile_s = (uint32_t)__cvta_generic_to_shared(tile);  // the tile's shared-window address
     __shared__ SmallPrimes sprimes;
     __shared__ unsigned long long s_seg;
-    __shared__ uint32_t s_iv, s_nsched, s_nsparse;
+    __shared__ uint32_t s_iv, s_nsparse;
+    // dense runs of warp w: s_runs[w][0 .. s_nruns[w]), each j | first round << 8 | rounds << 20
+    __shared__ uint32_t s_runs[NT / 32][kMaxRuns];
+    __shared__ uint32_t s_nruns[NT / 32];
 
     const uint32_t tid = threadIdx.x;
     const uint32_t lane = tid & 31, warp = tid >> 5;
@@ -201,55 +213,58 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
         sprimes.inv[t] = inv;
         sprimes.lim[t] = ~0ull / p;
     }
-    // Static strike schedule.  A prime power with at least two rounds of 32
-    // multiples per tile gets entries (j, c) of up to kRoundsPerEntry rounds
-    // each, a warp striking 32 consecutive multiples per round.  One with a
-    // single round (at most 32 multiples) gets one slot (j, m) per possible
-    // multiple m, and the slots of all of them are packed 32 to a warp pass, so
-    // that a warp pass is not spent on a handful of strikes.  The slots follow
-    // the entries in `sched`.
+    // Static strike schedule, built once per launch.
+    //  - Dense prime powers (at least two rounds of 32 multiples per tile): their rounds, in
+    //    order of j, are cut into NT/32 contiguous shares of equal length, one per warp.  A
+    //    warp's share is a list of runs (j, first round, rounds), each struck as consecutive
+    //    rounds of 32 multiples, so a warp sets up each prime power it touches once per tile.
+    //  - Single-round prime powers (at most 32 multiples per tile): one slot (j, m) per
+    //    possible multiple m, packed 32 to a warp pass in `sched`, so that a warp pass is not
+    //    spent on a handful of strikes.
     if (warp == 0) {
         constexpr int kPer = kMaxSpp / 32;
-        // entries (v) and slots (w) of prime power j
-        auto counts = [&](uint32_t j, uint32_t &v, uint32_t &w) {
-            const uint32_t rounds = j < nspp ? sdesc[j].w : 0u;
-            const bool single = rounds == 1;
-            v = rounds > 1 ? (rounds + kRoundsPerEntry - 1) / kRoundsPerEntry : 0;
-            w = single ? LT / sdesc[j].x + 1 : 0;  // at most 32
+        auto slots = [&](uint32_t j) -> uint32_t {  // at most 32
+            return j < nspp && sdesc[j].w == 1 ? LT / sdesc[j].x + 1 : 0u;
         };
-        uint32_t sum = 0, sumw = 0;
-        for (int u = 0; u < kPer; u++) {
-            uint32_t v, w;
-            counts(lane * kPer + u, v, w);
-            sum += v;
-            sumw += w;
-        }
-        uint32_t inc = sum, incw = sumw;
+        uint32_t sumw = 0;
+        for (int u = 0; u < kPer; u++) sumw += slots(lane * kPer + u);
+        uint32_t incw = sumw;
         for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t x = __shfl_up_sync(0xffffffffu, inc, o);
             const uint32_t y = __shfl_up_sync(0xffffffffu, incw, o);
-            if (lane >= (uint32_t)o) {
-                inc += x;
-                incw += y;
-            }
+            if (lane >= (uint32_t)o) incw += y;
         }
-        const uint32_t ndense = __shfl_sync(0xffffffffu, inc, 31);
-        uint32_t run = inc - sum, runw = ndense + incw - sumw;
+        uint32_t runw = incw - sumw;
         for (int u = 0; u < kPer; u++) {
-            const uint32_t j = lane * kPer + u;
-            uint32_t v, w;
-            counts(j, v, w);
-            for (uint32_t c = 0; c < v; c++)
-                if (run + c < P.n_sched) sched[run + c] = (uint16_t)(j | (c << 8));
+            const uint32_t j = lane * kPer + u, w = slots(j);
             for (uint32_t m = 0; m < w; m++)
                 if (runw + m < P.n_sched) sched[runw + m] = (uint16_t)(j | (m << 8));
-            run += v;
             runw += w;
         }
         if (lane == 31) {
-            s_nsched = inc < P.n_sched ? inc : P.n_sched;
-            s_nsparse = ndense + incw <= P.n_sched ? incw : 0u;  // n_sched always covers both
-            if (ndense + incw > P.n_sched && blockIdx.x == 0) atomicOr(&P.ctr->err, kErrSchedule);
+            s_nsparse = incw <= P.n_sched ? incw : 0u;  // n_sched always covers them
+            if (incw > P.n_sched && blockIdx.x == 0) atomicOr(&P.ctr->err, kErrSchedule);
+        }
+        // lane w < NT/32 lists the runs of warp w
+        if (lane < nwarps) {
+            uint32_t R = 0;
+            for (uint32_t j = 0; j < nspp; j++) {
+                const uint32_t r = sdesc[j].w;
+                if (r > 1) R += r;
+            }
+            const uint32_t b = (uint32_t)((uint64_t)R * lane / nwarps), e = (uint32_t)((uint64_t)R * (lane + 1) / nwarps);
+            uint32_t cs = 0, nr = 0;
+            for (uint32_t j = 0; j < nspp; j++) {
+                const uint32_t r = sdesc[j].w;
+                if (r < 2) continue;
+                const uint32_t lo = max(b, cs), hi = min(e, cs + r);
+                if (lo < hi) {
+                    if (nr < kMaxRuns) s_runs[lane][nr] = j | ((lo - cs) << 8) | ((hi - lo) << 20);
+                    nr++;
+                }
+                cs += r;
+            }
+            s_nruns[lane] = nr < kMaxRuns ? nr : kMaxRuns;
+            if (nr > kMaxRuns) atomicOr(&P.ctr->err, kErrSchedule);
         }
     }
 
@@ -275,8 +290,7 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
             sdesc[j].z = r ? q - r : 0;
         }
         for (uint32_t e = tid; e < nbc; e += NT) bcache[e] = pack_hit(P.bent[b0 + e]);
-        const uint32_t nsched = s_nsched, nsparse = s_nsparse;
-        const uint32_t nwork = nsched + (nsparse + 31) / 32;
+        const uint32_t nsparse = s_nsparse, nruns = s_nruns[warp];
         const uint32_t kinds = iv.kinds;
 
         for (uint32_t t0 = 0; t0 < seg_len; t0 += LT) {
@@ -305,40 +319,36 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
                 for (uint32_t i = tid; i < n4; i += NT) t4[i] = z;
             }
             __syncthreads();
-            for (uint32_t g = warp; g < nwork; g += nwarps) {
-                if (g < nsched) {
-                    const uint32_t e = sched[g];
-                    const uint32_t j = e & 255u;
-                    const uint32_t r0 = (e >> 8) * kRoundsPerEntry;
-                    const uint4 d = sdesc[j];
-                    const uint32_t q = d.x;
-                    const uint32_t reps = min(kRoundsPerEntry, d.w - r0);
-                    const uint32_t x = d.z + ((r0 << 5) + lane) * q;
-                    // 32q is a multiple of 4: x mod 4, hence the value's place in its word, is fixed
-                    // per lane.  The lane strikes x, x + 32q, ... up to xl, the last of its multiples
-                    // in this entry and in the tile; in words: up to the word of the largest value
-                    // <= xl congruent to x mod VPW.  For VPW <= 2 that bound cannot wrap (xl = 0
-                    // only when x = 0); for VPW = 4 the lanes with x > xl skip the entry.
-                    const uint32_t xl = min(tl, x + (reps - 1) * 32 * q);
-                    if (VPW < 4 || x <= xl) {
-                        const uint32_t lg = d.y << ((x & (VPW - 1)) * VBITS);
-                        uint32_t *a = &tile[x >> VSH];
-                        const uint32_t *alim = &tile[(xl - ((xl - x) & (VPW - 1))) >> VSH];
-                        const uint32_t wstep = (32 >> VSH) * q;
-#pragma unroll
-                        for (uint32_t r = 0; r < kRoundsPerEntry; r++, a += wstep) {
-                            if (a <= alim) atomicAdd(a, lg);
-                        }
+            // this warp's runs of dense rounds
+            for (uint32_t k = 0; k < nruns; k++) {
+                const uint32_t run = s_runs[warp][k];
+                const uint4 d = sdesc[run & 255u];
+                const uint32_t q = d.x, r0 = (run >> 8) & 0xfffu, reps = run >> 20;
+                const uint32_t x = d.z + ((r0 << 5) + lane) * q;
+                // 32q is a multiple of 4: x mod 4, hence the value's place in its word, is fixed
+                // per lane.  The lane strikes x, x + 32q, ... up to xl, the last of its multiples
+                // in this run and in the tile; in words: up to the word of the largest value
+                // <= xl congruent to x mod VPW.  For VPW <= 2 that bound cannot wrap (xl = 0
+                // only when x = 0); for VPW = 4 the lanes with x > xl skip the run.
+                const uint32_t xl = min(tl, x + (reps - 1) * 32 * q);
+                if (VPW < 4 || x <= xl) {
+                    const uint32_t lg = d.y << ((x & (VPW - 1)) * VBITS);
+                    uint32_t a = tile_s + ((x >> VSH) << 2);
+                    const uint32_t alim = tile_s + (((xl - ((xl - x) & (VPW - 1))) >> VSH) << 2);
+                    const uint32_t bstep = ((32 >> VSH) * q) << 2;
+#pragma unroll 4
+                    for (uint32_t r = 0; r < reps; r++, a += bstep) {
+                        if (a <= alim) red_add_shared(a, lg);
                     }
-                } else {  // packed slots of the single-round prime powers
-                    const uint32_t sl = (g - nsched) * 32 + lane;
-                    if (sl < nsparse) {
-                        const uint32_t e = sched[nsched + sl];
-                        const uint32_t j = e & 255u;
-                        const uint4 d = sdesc[j];
-                        const uint32_t x = d.z + (e >> 8) * d.x;
-                        if (x <= tl) atomicAdd(&tile[x >> VSH], d.y << ((x & (VPW - 1)) * VBITS));
-                    }
+                }
+            }
+            // packed slots of the single-round prime powers
+            for (uint32_t sl = warp * 32 + lane; sl < ((nsparse + 31) & ~31u); sl += NT) {
+                if (sl < nsparse) {
+                    const uint32_t e = sched[sl];
+                    const uint4 d = sdesc[e & 255u];
+                    const uint32_t x = d.z + (e >> 8) * d.x;
+                    if (x <= tl) red_add_shared(tile_s + ((x >> VSH) << 2), d.y << ((x & (VPW - 1)) * VBITS));
                 }
             }
             for (uint32_t e = tid; e < nbc; e += NT) {
@@ -347,7 +357,7 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
                 if (x <= tl) {
                     const uint32_t lg7 = w & 0xfffu;
                     const uint32_t lg = VB == 4 ? lg7 << 9 : VB == 2 ? lg7 << 1 : (lg7 + 63u) >> 6;
-                    atomicAdd(&tile[x >> VSH], lg << ((x & (VPW - 1)) * VBITS));
+                    red_add_shared(tile_s + ((x >> VSH) << 2), lg << ((x & (VPW - 1)) * VBITS));
                 }
             }
             for (unsigned long long e = b0 + nbc + tid; e < b1; e += NT) {
