@@ -35,10 +35,19 @@ UNIT = "integers/s"
 MAX_HI = (1 << 41) + (1 << 31)
 TUNE_CACHE = os.path.join(ROOT, "paper_2506_01099_gb300", "tune_cache.json")
 KERNELS_PER_STEP = 10  # plan, bucket count, 3 scan kernels, bucket fill, sieve, verify, sort, offsets
-# algorithmic integer lane-operations per searched integer ("Roofline"):
-#   init 1 + strikes 0.2732 * 5 + ctz 2 + key/filter 10  (odd prime powers: sum 1/(p(p-1)) = 0.2732)
-ALG_OPS_PER_INT = 1 + 0.2732 * 5 + 2 + 10
-SMS, LANES_PER_CLK, SM_MAX_MHZ = 152, 128, 2070.0
+# Algorithmic integer lane-operations per searched integer of each tile kind (the method as
+# built).  Strikes: sum over odd prime powers q = p^k, k >= 2, of 1/q
+# = sum_{p>=3} 1/(p(p-1)) = 0.2732 per integer, each an address step, a bound test and a
+# shared-memory reduction (3 ops).  Log tiles: the pair test of a word of VPW values is a
+# funnel shift, the pair add, the threshold add and the flag OR (4 ops per word), plus a
+# 16-byte load and a 16-byte clear per 16 bytes of tile.  The exact u64 tile: clear 1, strikes
+# as 64-bit multiplies (5 ops), 2-adic valuation 2, key and filter 10.
+STRIKE_OPS = 0.2732 * 3
+ALG_OPS_PER_INT = {3: STRIKE_OPS + 4 / 4 + 2 / 16,     # u8: 4 values per word, 16 per 16 bytes
+                   2: STRIKE_OPS + 4 / 2 + 2 / 8,      # u16
+                   0: STRIKE_OPS + 4 / 1 + 2 / 4,      # u32
+                   1: 1 + 0.2732 * 5 + 2 + 10}         # exact u64 tile
+SMS, LANES_PER_CLK, SCHEDULERS, SM_MAX_MHZ = 152, 128, 4, 2070.0
 
 
 def peaks():
@@ -105,9 +114,9 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
-def sieve_traffic(integers: int, tile_kind: int):
-    """DRAM bytes of one sieve launch, from the committed ncu capture of this tile
-    kind -- or None once the kernel source differs from the one that capture measured."""
+def sieve_record(tile_kind: int):
+    """The committed ncu record (DRAM bytes and warp instructions per integer) of the sieve
+    with this tile kind -- or None once the kernel source differs from the one it measured."""
     import glob
     import hashlib
 
@@ -127,7 +136,7 @@ def sieve_traffic(integers: int, tile_kind: int):
         return None
     if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
         return None
-    return rec["dram_bytes_per_integer"] * integers
+    return rec
 
 
 def load_tune(gpu_name: str) -> str | None:
@@ -366,8 +375,17 @@ def run_ours(args):
         pk, pk_src = peaks()
         ms_sieve = statistics.mean(sieve_ms)
         sieve_rate = integers / (ms_sieve / 1e3)
-        alu_peak = SMS * LANES_PER_CLK * float(pk.get("sm_max_mhz", SM_MAX_MHZ)) * 1e6 / 1e12
-        achieved = sieve_rate * ALG_OPS_PER_INT / 1e12
+        fmax = float(pk.get("sm_max_mhz", SM_MAX_MHZ))
+        alu_peak = SMS * LANES_PER_CLK * fmax * 1e6 / 1e12
+        tk = ctx.tune()["tile_kind"]
+        achieved = sieve_rate * ALG_OPS_PER_INT[tk] / 1e12
+        rec = sieve_record(tk)
+        issue = None
+        if rec is not None and rec.get("warp_inst_per_integer"):
+            # measured warp instructions of the kernel (ncu) per integer, against the issue limit
+            wipi = rec["warp_inst_per_integer"]
+            issue = {"warp_inst_per_integer": wipi, "frac": sieve_rate * wipi / (SMS * SCHEDULERS * fmax * 1e6),
+                     "note": "measured warp instructions x integers/s / (152 SMs x 4 schedulers x max clock)"}
         cpu = None
         if not args.no_cpu and ws == 1:
             cpu = cpu_baseline(W.batch_intervals(4096), int(args.cpu_budget))
@@ -387,13 +405,14 @@ def run_ours(args):
             "gpu_launches": KERNELS_PER_STEP * args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "Tops/s",
                          "frac": achieved / alu_peak,
-                         "traffic": sieve_traffic(integers, ctx.tune()["tile_kind"]),
+                         "traffic": rec["dram_bytes_per_integer"] * integers if rec else None,
                          "kernel": {0: "k_sieve_log<search, u32 tile>", 1: "k_sieve<search, exact u64 tile>",
                                     2: "k_sieve_log<search, u16 tile>",
                                     3: "k_sieve_log<search, u8 tile>"}[ctx.tune()["tile_kind"]]
                                    + " (persistent shared-memory tile sieve, fused filter + warp-ballot compaction)",
                          "peak_source": "152 SMs x 128 lanes/clk x max SM clock (issue roofline)",
-                         "alg_ops_per_integer": ALG_OPS_PER_INT, "sieve_ms_per_launch": ms_sieve,
+                         "alg_ops_per_integer": ALG_OPS_PER_INT[tk], "sieve_ms_per_launch": ms_sieve,
+                         "issue": issue,
                          "hbm_equivalent": {"achieved_gbs": sieve_rate * 8 / 1e9, "peak_gbs": pk["hbm_gbs"],
                                             "frac": sieve_rate * 8 / 1e9 / pk["hbm_gbs"],
                                             "note": f"8 B per integer vs {pk_src} copy bandwidth"}},
