@@ -34,7 +34,7 @@ METRIC = "integers searched/s at n~2^40, batched (4096 seeded intervals in [2^32
 UNIT = "integers/s"
 MAX_HI = (1 << 41) + (1 << 31)
 TUNE_CACHE = os.path.join(ROOT, "paper_2506_01099_gb300", "tune_cache.json")
-KERNELS_PER_STEP = 10  # plan, bucket count, 3 scan kernels, bucket fill, sieve, verify, sort, offsets
+KERNELS_PER_STEP = 11  # plan, bucket count, 3 scan kernels, bucket fill, sieve, exact check, verify, sort, offsets
 # Algorithmic integer lane-operations per searched integer of each tile kind (the method as
 # built).  Strikes: sum over odd prime powers q = p^k, k >= 2, of 1/q
 # = sum_{p>=3} 1/(p(p-1)) = 0.2732 per integer, each an address step, a bound test and a

@@ -60,9 +60,9 @@ struct bnx_ctx {
     std::vector<double> lq_inv;   // prefix sums of 1/q over lq
 
     // workspace
-    bnx::DevBuf ivs, n_iv, ctr, bcnt, boff, bent, scan_tmp, surv, pairs, pairs_sorted, offsets;
+    bnx::DevBuf ivs, n_iv, ctr, bcnt, boff, bent, scan_tmp, cand, surv, pairs, pairs_sorted, offsets;
     bnx::DevBuf hkeys, hheads, hnext, hslot;
-    size_t surv_want = 1 << 16, pair_want = 1 << 12;
+    size_t surv_want = 1 << 16, pair_want = 1 << 12, cand_want = 1 << 16;
     bnx::Counters *h_ctr = nullptr;  // pinned
     bnx::IvDev *h_ivs = nullptr;     // pinned staging
     size_t h_ivs_cap = 0;
@@ -96,7 +96,7 @@ struct bnx_ctx {
     bool server_running() const { return serving.load(); }
     std::vector<bnx::DevBuf *> all_bufs() {
         return {&primes, &spp,   &lpp,          &tmp_counts, &ivs,  &n_iv,  &ctr,  &bcnt,  &boff,  &bent,
-                &scan_tmp, &surv, &pairs, &pairs_sorted, &offsets, &hkeys, &hheads, &hnext, &hslot};
+                &scan_tmp, &cand, &surv, &pairs, &pairs_sorted, &offsets, &hkeys, &hheads, &hnext, &hslot};
     }
 };
 

@@ -10,6 +10,7 @@
 //   ivs         IvDev[k]         the intervals with their segment and chunk bases
 //   bcnt/boff   u32/u64          bucket sizes and offsets per queue segment
 //   bent        uint2[]          bucket entries (value offset in segment, prime)
+//   cand        Cand[]           log-tile candidates left for the exact check (compacted)
 //   surv        Survivor[]       n passing a necessary condition (compacted)
 //   pairs       PairDev[]        verified pairs, then sorted
 #pragma once
@@ -57,6 +58,17 @@ struct Survivor {
     uint32_t iv;
 };
 
+// A log-tile candidate whose bound still reaches the threshold with its exact power
+// of 2: the exact square parts and the per-kind conditions decide (k_cand).
+struct Cand {
+    uint64_t n;
+    uint64_t b0;     // its segment's bucket entries: bent[b0 .. b0 + nb)
+    uint32_t nb;
+    uint32_t o;      // offset of n in its segment
+    uint32_t kinds;  // the interval's kinds
+    uint32_t iv;
+};
+
 struct PairDev {
     uint64_t m, n;
     uint32_t kind, iv;
@@ -69,6 +81,7 @@ struct Counters {
     unsigned long long n_pairs;      // pairs written (may exceed capacity)
     unsigned long long bucket_hits;
     unsigned long long surv1, surv2, candidates, hash_keys;
+    unsigned long long n_cand;       // log-tile candidates written (may exceed capacity)
     unsigned long long total_segs, total_chunks;  // plan totals
     unsigned int err;                // nonzero: a device-side limit was hit
     unsigned int pad;
@@ -80,6 +93,7 @@ constexpr unsigned kErrPairOverflow = 2u;
 constexpr unsigned kErrBucketOverflow = 4u;
 constexpr unsigned kErrHashFull = 8u;
 constexpr unsigned kErrSchedule = 32u;  // a strike schedule did not fit its array (never expected)
+constexpr unsigned kErrCandOverflow = 64u;
 
 // Everything a pipeline's kernels read.  Passed by value to every launch; the
 // sizes that vary per run live in device memory (Counters, IvDev) so that one
@@ -103,6 +117,8 @@ struct Plan {
     Counters *ctr;
     Survivor *surv;
     uint64_t surv_cap;
+    Cand *cand;
+    uint64_t cand_cap;
     PairDev *pairs;
     PairDev *pairs_sorted;
     uint64_t pair_cap;
@@ -147,6 +163,8 @@ int sieve_occupancy(int mode, int threads, size_t smem, int *ctas_per_sm);
 // vb: bytes per tile value (4, 2 or 1)
 void launch_sieve_log(const Plan &P, int mode, int vb, int grid, int threads, size_t smem, cudaStream_t s);
 int sieve_log_occupancy(int mode, int threads, int vb, size_t smem, int *ctas_per_sm);
+// exact check of the log tile's candidates: survivors into P.surv
+void launch_cand(const Plan &P, int mode, int grid, cudaStream_t s);
 size_t sieve_log_smem_bytes(uint32_t tile_log2, uint32_t nspp, uint32_t nsched, int vb);
 size_t sieve_smem_bytes(uint32_t tile_log2, uint32_t nspp, uint32_t nsched);
 uint32_t sched_length(uint32_t tile_log2, const uint32_t *q, uint32_t nspp);

@@ -217,6 +217,7 @@ int ensure_ws(bnx_ctx *c, const PlanTotals &t, size_t k) {
     if ((rc = need(c->boff, sizeof(unsigned long long) * (t.segs + 2)))) return rc;
     if ((rc = need(c->scan_tmp, sizeof(unsigned long long) * (t.segs / 4096 + 2)))) return rc;
     if ((rc = need(c->bent, sizeof(uint2) * (t.buckets + 1)))) return rc;
+    if ((rc = need(c->cand, sizeof(Cand) * c->cand_want))) return rc;
     if ((rc = need(c->surv, sizeof(Survivor) * c->surv_want))) return rc;
     if ((rc = need(c->pairs, sizeof(PairDev) * c->pair_want))) return rc;
     if ((rc = need(c->pairs_sorted, sizeof(PairDev) * c->pair_want))) return rc;
@@ -267,6 +268,8 @@ Plan make_plan(const bnx_ctx *c) {
     P.ctr = (Counters *)c->ctr.p;
     P.surv = (Survivor *)c->surv.p;
     P.surv_cap = c->surv.bytes / sizeof(Survivor);
+    P.cand = (Cand *)c->cand.p;
+    P.cand_cap = c->cand.bytes / sizeof(Cand);
     P.pairs = (PairDev *)c->pairs.p;
     P.pairs_sorted = (PairDev *)c->pairs_sorted.p;
     P.pair_cap = c->pairs.bytes / sizeof(PairDev);
@@ -352,6 +355,7 @@ int record_pipeline(bnx_ctx *c, int mode, cudaStream_t s, bool timing) {
     if (use_log_tile(c, mode)) launch_sieve_log(P, mode, log_vb(c), sgrid, sthreads, ssmem, s);
     else launch_sieve(P, mode, sgrid, sthreads, ssmem, s);
     if (timing) CUDA_TRY(cudaEventRecordWithFlags(c->ev_s1, s, c->capturing ? cudaEventRecordExternal : 0));
+    if (use_log_tile(c, mode)) launch_cand(P, mode, c->n_sm * 2, s);
     if (mode == kModeSearch) {
         launch_verify(P, c->n_sm * 4, s);
         launch_sort(P, c->n_sm * 2, s);
@@ -411,8 +415,9 @@ int run_search(bnx_ctx *c, size_t k, bool use_graph) {
 int check_counters(bnx_ctx *c, bool *rerun) {
     *rerun = false;
     const Counters &h = *c->h_ctr;
-    if (h.err & (kErrSurvOverflow | kErrPairOverflow)) {
+    if (h.err & (kErrSurvOverflow | kErrPairOverflow | kErrCandOverflow)) {
         if (h.n_surv > c->surv.bytes / sizeof(Survivor)) c->surv_want = (size_t)(h.n_surv + h.n_surv / 2 + 1024);
+        if (h.n_cand > c->cand.bytes / sizeof(Cand)) c->cand_want = (size_t)(h.n_cand + h.n_cand / 2 + 1024);
         if (h.n_pairs > c->pairs.bytes / sizeof(PairDev)) c->pair_want = (size_t)(h.n_pairs + h.n_pairs / 2 + 1024);
         *rerun = true;
         return BNX_E_OVERFLOW;
@@ -724,8 +729,9 @@ int bnx_search_hash(bnx_ctx *c, uint64_t S, uint32_t kinds, bnx_pair *out, size_
         CUDA_TRY(cudaEventRecord(c->ev0, s));
         if ((rc = record_pipeline(c, kModeHash, s, true))) return rc;
         CUDA_TRY(cudaStreamSynchronize(s));
-        if (c->h_ctr->err & kErrSurvOverflow) {
-            c->surv_want = (size_t)(c->h_ctr->n_surv + c->h_ctr->n_surv / 2 + 1024);
+        if (c->h_ctr->err & (kErrSurvOverflow | kErrCandOverflow)) {
+            if (c->h_ctr->err & kErrSurvOverflow) c->surv_want = (size_t)(c->h_ctr->n_surv + c->h_ctr->n_surv / 2 + 1024);
+            if (c->h_ctr->err & kErrCandOverflow) c->cand_want = (size_t)(c->h_ctr->n_cand + c->h_ctr->n_cand / 2 + 1024);
             continue;
         }
         if (c->h_ctr->err) return fail(BNX_E_OVERFLOW, "device capacity exceeded (flags 0x%x)", c->h_ctr->err);

@@ -179,7 +179,6 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
     uint16_t *sched = reinterpret_cast<uint16_t *>(smem_raw + lay.sched);
     uint32_t *bcache = reinterpret_cast<uint32_t *>(smem_raw + lay.bcache);
     const uint32_t tile_s = (uint32_t)__cvta_generic_to_shared(tile);  // the tile's shared-window address
-    __shared__ SmallPrimes sprimes;
     __shared__ unsigned long long s_seg;
     __shared__ uint32_t s_iv, s_nsparse;
     // dense runs of warp w: s_runs[w][0 .. s_nruns[w]), each j | first round << 8 | rounds << 20
@@ -198,21 +197,7 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
         sdesc[j] = make_uint4(e.q, lg, 0u, (LT / e.q + 1 + 31) / 32);  // at most floor(L_tile/q)+1 multiples of q
         slmod[j] = LT % e.q;
     }
-    if (tid == 0) {
-        // distinct in-tile primes (their square is an in-tile prime power)
-        uint32_t c = 0;
-        for (uint32_t j = 0; j < nspp && c < kMaxSmallPrimes; j++)
-            if (P.spp[j].k == 2) sprimes.p[c++] = P.spp[j].p;
-        sprimes.n = c;
-    }
     __syncthreads();
-    for (uint32_t t = tid; t < sprimes.n; t += NT) {
-        const unsigned long long p = sprimes.p[t];
-        unsigned long long inv = p;  // Newton: each step doubles the correct low bits
-        for (int it = 0; it < 6; it++) inv *= 2ull - p * inv;
-        sprimes.inv[t] = inv;
-        sprimes.lim[t] = ~0ull / p;
-    }
     // Static strike schedule, built once per launch.
     //  - Dense prime powers (at least two rounds of 32 multiples per tile): their rounds, in
     //    order of j, are cut into NT/32 contiguous shares of equal length, one per warp.  A
@@ -441,13 +426,16 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
                         }
                     }
                 }
+                // candidates whose bound, with the exact power of 2 of P, still reaches the
+                // threshold go to the exact check (k_cand): about 2 per 2^23 integers near 2^40
                 while (__any_sync(0xffffffffu, cm != 0)) {
-                    uint32_t kk = 0;
-                    uint64_t n = 0, a = 0, b = 0;
+                    bool defer = false;
+                    uint64_t n = 0;
+                    uint32_t i = 0;
                     if (cm) {
                         const uint32_t u = (uint32_t)(__ffs(cm) - 1);
                         cm &= cm - 1;
-                        const uint32_t i = G * g + u;
+                        i = G * g + u;
                         n = t_lo + i;
                         const uint32_t e2 = ctz64(n + (n & 1)) - 1;  // power of 2 in P
                         const uint32_t L0 = (tile[i >> VSH] >> ((i & (VPW - 1)) * VBITS)) & VMASK;
@@ -461,36 +449,96 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
                             need = (int)flog2_64(n) + (int)flog2_64(n + 1) - (int)flog2_64(S2) -
                                    ((S2 & (S2 - 1)) ? 1 : 0);
                         }
-                        if (ub >= (int64_t)need * FS) {
-                            const uint64_t s0 = sodd_exact(n, t0 + i, &sprimes, P.sqrt_q, P.bent, b0, b1);
-                            const uint64_t s1 = sodd_exact(n + 1, t0 + i + 1, &sprimes, P.sqrt_q, P.bent, b0, b1);
-                            kk = exact_kinds_log(n, s0, s1, kinds, MODE, P.hash_S, &a, &b);
-                        }
+                        defer = ub >= (int64_t)need * FS;
                     }
-                    const uint32_t m = __ballot_sync(0xffffffffu, kk != 0);  // warp-ballot compaction
+                    const uint32_t m = __ballot_sync(0xffffffffu, defer);  // warp-ballot compaction
                     if (m) {
                         unsigned long long wbase = 0;
-                        if (lane == 0) wbase = atomicAdd(&P.ctr->n_surv, (unsigned long long)__popc(m));
+                        if (lane == 0) wbase = atomicAdd(&P.ctr->n_cand, (unsigned long long)__popc(m));
                         wbase = __shfl_sync(0xffffffffu, wbase, 0);
-                        if (kk) {
+                        if (defer) {
                             const unsigned long long at = wbase + __popc(m & ((1u << lane) - 1));
-                            if (at < P.surv_cap) {
-                                Survivor sv;
-                                sv.n = n;
-                                sv.a = a;
-                                sv.b = b;
-                                sv.kinds = kk;
-                                sv.iv = s_iv;
-                                P.surv[at] = sv;
+                            if (at < P.cand_cap) {
+                                Cand cd;
+                                cd.n = n;
+                                cd.b0 = b0;
+                                cd.nb = (uint32_t)(b1 - b0);
+                                cd.o = t0 + i;
+                                cd.kinds = kinds;
+                                cd.iv = s_iv;
+                                P.cand[at] = cd;
                             } else {
-                                atomicOr(&P.ctr->err, kErrSurvOverflow);
-                            }
-                            if (MODE == kModeSearch) {
-                                if (kk & 1) atomicAdd(&P.ctr->surv1, 1ull);
-                                if (kk & 2) atomicAdd(&P.ctr->surv2, 1ull);
+                                atomicOr(&P.ctr->err, kErrCandOverflow);
                             }
                         }
                     }
+                }
+            }
+        }
+    }
+}
+
+// Exact check of the log tile's candidates (one thread each; they are rare): the odd
+// square parts of n and n+1 by exact-division tests with the in-tile primes and by the
+// segment's bucket entries, then the exact 128-bit per-kind conditions.  Survivors are
+// compacted into P.surv, as the exact tile's sieve writes them.
+template <int MODE>
+__global__ void __launch_bounds__(256) k_cand(Plan P) {
+    __shared__ SmallPrimes sprimes;
+    const uint32_t tid = threadIdx.x, lane = tid & 31;
+    if (tid == 0) {
+        // distinct in-tile primes (their square is an in-tile prime power)
+        uint32_t c = 0;
+        for (uint32_t j = 0; j < P.n_spp && c < kMaxSmallPrimes; j++)
+            if (P.spp[j].k == 2) sprimes.p[c++] = P.spp[j].p;
+        sprimes.n = c;
+    }
+    __syncthreads();
+    for (uint32_t t = tid; t < sprimes.n; t += blockDim.x) {
+        const unsigned long long p = sprimes.p[t];
+        unsigned long long inv = p;  // Newton: each step doubles the correct low bits
+        for (int it = 0; it < 6; it++) inv *= 2ull - p * inv;
+        sprimes.inv[t] = inv;
+        sprimes.lim[t] = ~0ull / p;
+    }
+    __syncthreads();
+    const unsigned long long nc = min(P.ctr->n_cand, (unsigned long long)P.cand_cap);
+    const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
+    for (unsigned long long base = (unsigned long long)blockIdx.x * blockDim.x + (tid & ~31u); base < nc;
+         base += stride) {
+        const unsigned long long c = base + lane;
+        uint32_t kk = 0, iv = 0;
+        uint64_t n = 0, a = 0, b = 0;
+        if (c < nc) {
+            const Cand cd = P.cand[c];
+            n = cd.n;
+            iv = cd.iv;
+            const unsigned long long ge = cd.b0 + cd.nb;
+            const uint64_t s0 = sodd_exact(n, cd.o, &sprimes, P.sqrt_q, P.bent, cd.b0, ge);
+            const uint64_t s1 = sodd_exact(n + 1, cd.o + 1, &sprimes, P.sqrt_q, P.bent, cd.b0, ge);
+            kk = exact_kinds_log(n, s0, s1, cd.kinds, MODE, P.hash_S, &a, &b);
+        }
+        const uint32_t m = __ballot_sync(0xffffffffu, kk != 0);  // warp-ballot compaction
+        if (m) {
+            unsigned long long wbase = 0;
+            if (lane == 0) wbase = atomicAdd(&P.ctr->n_surv, (unsigned long long)__popc(m));
+            wbase = __shfl_sync(0xffffffffu, wbase, 0);
+            if (kk) {
+                const unsigned long long at = wbase + __popc(m & ((1u << lane) - 1));
+                if (at < P.surv_cap) {
+                    Survivor sv;
+                    sv.n = n;
+                    sv.a = a;
+                    sv.b = b;
+                    sv.kinds = kk;
+                    sv.iv = iv;
+                    P.surv[at] = sv;
+                } else {
+                    atomicOr(&P.ctr->err, kErrSurvOverflow);
+                }
+                if (MODE == kModeSearch) {
+                    if (kk & 1) atomicAdd(&P.ctr->surv1, 1ull);
+                    if (kk & 2) atomicAdd(&P.ctr->surv2, 1ull);
                 }
             }
         }
@@ -527,6 +575,11 @@ int sieve_log_occupancy(int mode, int threads, int vb, size_t smem, int *ctas_pe
     cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return (int)e;
     return (int)cudaOccupancyMaxActiveBlocksPerMultiprocessor(ctas_per_sm, fn, threads, smem);
+}
+
+void launch_cand(const Plan &P, int mode, int grid, cudaStream_t s) {
+    if (mode == kModeHash) k_cand<kModeHash><<<grid, 256, 0, s>>>(P);
+    else k_cand<kModeSearch><<<grid, 256, 0, s>>>(P);
 }
 
 void launch_sieve_log(const Plan &P, int mode, int vb, int grid, int threads, size_t smem, cudaStream_t s) {
