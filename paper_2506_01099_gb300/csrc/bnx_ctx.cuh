@@ -60,7 +60,7 @@ struct bnx_ctx {
     std::vector<double> lq_inv;   // prefix sums of 1/q over lq
 
     // workspace
-    bnx::DevBuf ivs, n_iv, ctr, bcnt, boff, bent, scan_tmp, cand, surv, pairs, pairs_sorted, offsets;
+    bnx::DevBuf ivs, n_iv, ctr, bcnt, seg_iv, boff, bent, scan_tmp, cand, surv, pairs, pairs_sorted, offsets;
     bnx::DevBuf hkeys, hheads, hnext, hslot;
     size_t surv_want = 1 << 16, pair_want = 1 << 12, cand_want = 1 << 16;
     bnx::Counters *h_ctr = nullptr;  // pinned
@@ -95,7 +95,7 @@ struct bnx_ctx {
     uint32_t chunk_log2() const { return seg_log2() + bnx::kChunkSegsLog2; }
     bool server_running() const { return serving.load(); }
     std::vector<bnx::DevBuf *> all_bufs() {
-        return {&primes, &spp,   &lpp,          &tmp_counts, &ivs,  &n_iv,  &ctr,  &bcnt,  &boff,  &bent,
+        return {&primes, &spp,   &lpp,          &tmp_counts, &ivs,  &n_iv,  &ctr,  &bcnt,  &seg_iv, &boff,  &bent,
                 &scan_tmp, &cand, &surv, &pairs, &pairs_sorted, &offsets, &hkeys, &hheads, &hnext, &hslot};
     }
 };

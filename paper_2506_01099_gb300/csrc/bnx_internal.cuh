@@ -9,6 +9,7 @@
 // Per pipeline run (workspace, grown on demand):
 //   ivs         IvDev[k]         the intervals with their segment and chunk bases
 //   bcnt/boff   u32/u64          bucket sizes and offsets per queue segment
+//   seg_iv      u32              interval of each queue segment
 //   bent        uint2[]          bucket entries (value offset in segment, prime)
 //   cand        Cand[]           log-tile candidates left for the exact check (compacted)
 //   surv        Survivor[]       n passing a necessary condition (compacted)
@@ -111,6 +112,7 @@ struct Plan {
     uint32_t tile_log2, seg_log2;  // tile 2^tile_log2 integers, queue segment 2^seg_log2
     uint32_t chunk_log2;           // bucket-fill chunk: 2^chunk_log2 sieved values
     uint32_t *bcnt;                // [seg capacity]
+    uint32_t *seg_iv;              // [seg capacity] interval of each queue segment (written by the bucket count)
     unsigned long long *boff;      // [seg capacity + 1]
     uint2 *bent;                   // [bucket capacity]
     uint64_t seg_cap, bucket_cap;

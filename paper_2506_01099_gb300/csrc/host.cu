@@ -214,6 +214,7 @@ int ensure_ws(bnx_ctx *c, const PlanTotals &t, size_t k) {
     if ((rc = need(c->ivs, sizeof(IvDev) * (k + 1)))) return rc;
     if ((rc = need(c->offsets, sizeof(uint64_t) * (k + 2)))) return rc;
     if ((rc = need(c->bcnt, sizeof(uint32_t) * (t.segs + 1)))) return rc;
+    if ((rc = need(c->seg_iv, sizeof(uint32_t) * (t.segs + 1)))) return rc;
     if ((rc = need(c->boff, sizeof(unsigned long long) * (t.segs + 2)))) return rc;
     if ((rc = need(c->scan_tmp, sizeof(unsigned long long) * (t.segs / 4096 + 2)))) return rc;
     if ((rc = need(c->bent, sizeof(uint2) * (t.buckets + 1)))) return rc;
@@ -258,10 +259,12 @@ Plan make_plan(const bnx_ctx *c) {
         P.n_lpp_dense = (uint32_t)(std::upper_bound(c->lq.begin(), c->lq.end(), qd) - c->lq.begin());
     }
     P.bcnt = (uint32_t *)c->bcnt.p;
+    P.seg_iv = (uint32_t *)c->seg_iv.p;
     P.boff = (unsigned long long *)c->boff.p;
     P.bent = (uint2 *)c->bent.p;
     {
-        const uint64_t a = c->bcnt.bytes / sizeof(uint32_t), b = c->boff.bytes / sizeof(unsigned long long);
+        const uint64_t a = std::min(c->bcnt.bytes, c->seg_iv.bytes) / sizeof(uint32_t),
+                       b = c->boff.bytes / sizeof(unsigned long long);
         P.seg_cap = std::min(a > 0 ? a - 1 : 0, b > 1 ? b - 2 : 0);
     }
     P.bucket_cap = c->bent.bytes / sizeof(uint2);

@@ -167,6 +167,7 @@ __global__ void __launch_bounds__(256) k_bucket(Plan P) {
         for (uint32_t i = threadIdx.x; i < kChunkSegs; i += blockDim.x) {
             hist[i] = 0;
             if (FILL && i < nsc) sbase[i] = P.boff[iv.seg_base + s_first + i];
+            if (!FILL && i < nsc) P.seg_iv[iv.seg_base + s_first + i] = s_iv;  // for the sieve's queue
         }
         __syncthreads();
         // dense prime powers: a warp per q, lanes on consecutive multiples

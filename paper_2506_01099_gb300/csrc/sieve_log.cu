@@ -50,18 +50,6 @@ __device__ __forceinline__ void red_add_shared(uint32_t addr, uint32_t v) {
 __device__ __forceinline__ uint32_t ctz64(uint64_t x) { return (uint32_t)(__ffsll((long long)x) - 1); }
 __device__ __forceinline__ uint32_t flog2_64(uint64_t x) { return 63u - (uint32_t)__clzll((long long)x); }
 
-template <bool SEG>
-__device__ __forceinline__ uint32_t find_iv(const IvDev *ivs, uint32_t k, uint64_t x) {
-    uint32_t lo = 0, hi = k;
-    while (hi - lo > 1) {
-        const uint32_t mid = (lo + hi) >> 1;
-        const uint64_t b = SEG ? ivs[mid].seg_base : ivs[mid].chunk_base;
-        if (b <= x) lo = mid;
-        else hi = mid;
-    }
-    return lo;
-}
-
 struct LogLayout {
     size_t tile, spp, sched, bcache, total;
 };
@@ -179,7 +167,9 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
     uint16_t *sched = reinterpret_cast<uint16_t *>(smem_raw + lay.sched);
     uint32_t *bcache = reinterpret_cast<uint32_t *>(smem_raw + lay.bcache);
     const uint32_t tile_s = (uint32_t)__cvta_generic_to_shared(tile);  // the tile's shared-window address
-    __shared__ unsigned long long s_seg;
+    // the CTA's next queue segment: index, interval, interval record and bucket range
+    __shared__ unsigned long long s_seg, s_b0, s_b1;
+    __shared__ IvDev s_ivd;
     __shared__ uint32_t s_iv, s_nsparse;
     // dense runs of warp w: s_runs[w][0 .. s_nruns[w]), each j | first round << 8 | rounds << 20
     __shared__ uint32_t s_runs[NT / 32][kMaxRuns];
@@ -189,7 +179,8 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
     const uint32_t lane = tid & 31, warp = tid >> 5;
     constexpr uint32_t nwarps = NT / 32;
     const uint32_t k = *P.n_iv;
-    const unsigned long long total_segs = P.ctr->total_segs;
+    // (segments beyond the workspace's capacity are never planned: the bucket count flags them)
+    const unsigned long long total_segs = min(P.ctr->total_segs, (unsigned long long)P.seg_cap);
 
     for (uint32_t j = tid; j < nspp; j += NT) {
         const SmallPP e = P.spp[j];
@@ -253,20 +244,31 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
         }
     }
 
-    for (;;) {
-        __syncthreads();
-        if (tid == 0) {
-            s_seg = atomicAdd(&P.ctr->queue_head, 1ull);
-            s_iv = s_seg < total_segs ? find_iv<true>(P.ivs, k, s_seg) : 0;
+    // Work queue: a CTA pops its next segment while it sieves the current one (the pop's
+    // latency is hidden), and looks up its interval in the segment map at the end.
+    auto fetch = [&](unsigned long long sg) {  // one thread
+        s_seg = sg;
+        if (sg < total_segs) {
+            const uint32_t i = min(P.seg_iv[sg], k - 1);
+            s_iv = i;
+            s_ivd = P.ivs[i];
+            s_b0 = P.boff[sg];
+            s_b1 = P.boff[sg + 1];
         }
+    };
+    if (tid == 0) fetch(atomicAdd(&P.ctr->queue_head, 1ull));
+    for (;;) {
         __syncthreads();
         const unsigned long long seg = s_seg;
         if (seg >= total_segs) break;
-        const IvDev iv = P.ivs[s_iv];
+        const uint32_t ivi = s_iv;
+        const IvDev iv = s_ivd;
+        const unsigned long long b0 = s_b0, b1 = s_b1;
+        unsigned long long nxt = 0;
+        if (tid == NT - 1) nxt = atomicAdd(&P.ctr->queue_head, 1ull);
         const uint64_t seg_lo = iv.lo + ((seg - iv.seg_base) << P.seg_log2);
         const uint64_t rem = iv.hi - seg_lo;
         const uint32_t seg_len = rem < (1ull << P.seg_log2) ? (uint32_t)rem : (1u << P.seg_log2);
-        const unsigned long long b0 = P.boff[seg], b1 = P.boff[seg + 1];
         const unsigned long long ncache = P.seg_log2 <= 19 ? (unsigned long long)kLogBucketCache : 0ull;
         const uint32_t nbc = (uint32_t)((b1 - b0) < ncache ? (b1 - b0) : ncache);
         for (uint32_t j = tid; j < nspp; j += NT) {
@@ -465,7 +467,7 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
                                 cd.nb = (uint32_t)(b1 - b0);
                                 cd.o = t0 + i;
                                 cd.kinds = kinds;
-                                cd.iv = s_iv;
+                                cd.iv = ivi;
                                 P.cand[at] = cd;
                             } else {
                                 atomicOr(&P.ctr->err, kErrCandOverflow);
@@ -475,6 +477,8 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
                 }
             }
         }
+        // every thread has read s_seg .. s_b1 (a barrier of the tile loop lies between)
+        if (tid == NT - 1) fetch(nxt);
     }
 }
 
