@@ -182,11 +182,32 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
     // (segments beyond the workspace's capacity are never planned: the bucket count flags them)
     const unsigned long long total_segs = min(P.ctr->total_segs, (unsigned long long)P.seg_cap);
 
+    // u8 tile: the strikes of 9, 27 and 81 repeat with period 81.  Their sum at n is
+    // lg(3) * #{k in 2..4 : 3^k | n}, and a tile word holds the values n .. n+3, so the word
+    // is a function of n mod 81 alone (gcd(4, 81) = 1 makes every residue occur): the tile
+    // is initialised from that 81-word table instead of zeros, and 9, 27, 81 leave the
+    // strike schedule.
+    constexpr bool kPat = VB == 1;
+    // entry r': the words of residues r, r+4, r+8, r+12 for r = 16 r' mod 81, so that the
+    // consecutive 16-byte stores of a warp (16 values apart) read consecutive entries
+    __shared__ uint4 s_pat[kPat ? 81 : 1];
     for (uint32_t j = tid; j < nspp; j += NT) {
         const SmallPP e = P.spp[j];
         const uint32_t lg = VB == 4 ? e.lg : (uint32_t)floor(log2((double)e.p) * (double)FS) + 1u;
-        sdesc[j] = make_uint4(e.q, lg, 0u, (LT / e.q + 1 + 31) / 32);  // at most floor(L_tile/q)+1 multiples of q
+        const bool in_pat = kPat && (e.q == 9 || e.q == 27 || e.q == 81);
+        // rounds: at most floor(L_tile/q)+1 multiples of q per tile; 0 = not in the schedule
+        sdesc[j] = make_uint4(e.q, lg, 0u, in_pat ? 0u : (LT / e.q + 1 + 31) / 32);
         slmod[j] = LT % e.q;
+    }
+    if (kPat && tid < 81) {
+        const uint32_t lg3 = (uint32_t)floor(log2(3.0) * (double)FS) + 1u;
+        uint32_t w[4] = {0, 0, 0, 0};
+        for (uint32_t c = 0; c < 4; c++)
+            for (uint32_t b = 0; b < 4; b++) {
+                const uint32_t m = (16 * tid + 4 * c + b) % 81;
+                w[c] |= lg3 * ((m % 9 == 0) + (m % 27 == 0) + (m == 0)) << (8 * b);
+            }
+        s_pat[tid] = make_uint4(w[0], w[1], w[2], w[3]);
     }
     __syncthreads();
     // Static strike schedule, built once per launch.
@@ -303,7 +324,19 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
                 // values [0, tl] and the slack after them (the epilogue's reads past tl see only
                 // zeros or values of earlier tiles; either only adds candidates, which are masked)
                 const uint32_t n4 = VB == 4 ? ((tl + 4) >> 2) + 1 : ((tl >> VSH) + 8 + 3) >> 2;
-                for (uint32_t i = tid; i < n4; i += NT) t4[i] = z;
+                if constexpr (kPat) {
+                    // word w of the tile starts at n = t_lo + 4w: store i (words 4i ..) starts at
+                    // t_lo + 16 i, whose entry is r' = (t_lo + 16 i) / 16 mod 81 = 76 t_lo + i
+                    // (16 * 76 = 1 mod 81)
+                    constexpr uint32_t kStep = NT % 81u;
+                    uint32_t r = (uint32_t)((t_lo * 76ull + tid) % 81ull);
+                    for (uint32_t i = tid; i < n4; i += NT) {
+                        t4[i] = s_pat[r];
+                        r = r + kStep >= 81 ? r + kStep - 81 : r + kStep;
+                    }
+                } else {
+                    for (uint32_t i = tid; i < n4; i += NT) t4[i] = z;
+                }
             }
             __syncthreads();
             // this warp's runs of dense rounds
