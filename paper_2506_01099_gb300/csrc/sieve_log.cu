@@ -26,15 +26,19 @@ namespace bnx {
 
 namespace {
 
-// A segment's bucket entries are cached in shared memory, each packed into one
+// The first 512 bucket entries of a segment (a segment of 2^18 values near 2^40
+// holds about 280 at Q = 2^15) are cached in shared memory, each packed into one
 // word: (offset in the segment) << 12 | lg7, lg7 = ceil(log2 p * 2^7) with
 // margin (p < 2^22: lg7 < 2^12).  Offsets reach the segment length, so the
-// cache is used for segments of at most 2^19 values; larger segments read all
-// their entries from global memory.  A strike
+// cache is used for segments of at most 2^19 values; the entries of larger
+// segments, and those beyond the cache, are read from global memory.  A strike
 // adds lg7 << 9 to the u32 tile (units 2^-16), lg7 << 1 to the u16 tile (units
 // 2^-8) or ceil(lg7 / 2^6) to the u8 tile (units 2^-1): an over-estimate of
 // log2 p, as the rejection rule needs.
-constexpr int kLogBucketCache = 1024;
+constexpr int kLogBucketCache = 512;
+// The cached entries are then binned by tile (bsort), so that a tile reads only its own;
+// an entry on a tile boundary (x = L_tile of one tile, x = 0 of the next) is in both bins.
+constexpr uint32_t kMaxSegTiles = 64;
 constexpr uint32_t kHigh2 = 16;
 constexpr int kMaxSmallPrimes = 64;
 // Runs of dense strike rounds per warp (a warp's equal share of all dense rounds of a tile
@@ -51,7 +55,7 @@ __device__ __forceinline__ uint32_t ctz64(uint64_t x) { return (uint32_t)(__ffsl
 __device__ __forceinline__ uint32_t flog2_64(uint64_t x) { return 63u - (uint32_t)__clzll((long long)x); }
 
 struct LogLayout {
-    size_t tile, spp, sched, bcache, total;
+    size_t tile, spp, sched, bcache, bsort, total;
 };
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -65,7 +69,8 @@ __host__ __device__ inline LogLayout log_layout(uint32_t tile_log2, uint32_t nsp
     L.spp = al16(words * sizeof(uint32_t));
     L.sched = L.spp + al16((size_t)5 * (nspp ? nspp : 1) * sizeof(uint32_t));
     L.bcache = L.sched + al16((size_t)(nsched ? nsched : 1) * sizeof(uint16_t));
-    L.total = L.bcache + (size_t)kLogBucketCache * sizeof(uint32_t);
+    L.bsort = L.bcache + (size_t)kLogBucketCache * sizeof(uint32_t);
+    L.total = L.bsort + (size_t)(kLogBucketCache + kMaxSegTiles) * sizeof(uint32_t);
     return L;
 }
 
@@ -166,6 +171,9 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
     uint32_t *slmod = reinterpret_cast<uint32_t *>(sdesc + nspp);  // L_tile mod q
     uint16_t *sched = reinterpret_cast<uint16_t *>(smem_raw + lay.sched);
     uint32_t *bcache = reinterpret_cast<uint32_t *>(smem_raw + lay.bcache);
+    uint32_t *bsort = reinterpret_cast<uint32_t *>(smem_raw + lay.bsort);
+    // per-tile bins of the cached bucket entries: starts, and counts / write cursors
+    __shared__ uint32_t s_bstart[kMaxSegTiles + 1], s_bcnt[kMaxSegTiles + 1];
     const uint32_t tile_s = (uint32_t)__cvta_generic_to_shared(tile);  // the tile's shared-window address
     // the CTA's next queue segment: index, interval, interval record and bucket range
     __shared__ unsigned long long s_seg, s_b0, s_b1;
@@ -278,6 +286,7 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
         }
     };
     if (tid == 0) fetch(atomicAdd(&P.ctr->queue_head, 1ull));
+    if (tid <= kMaxSegTiles) s_bcnt[tid] = 0;
     for (;;) {
         __syncthreads();
         const unsigned long long seg = s_seg;
@@ -297,7 +306,35 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
             const uint32_t r = (uint32_t)(seg_lo % q);
             sdesc[j].z = r ? q - r : 0;
         }
-        for (uint32_t e = tid; e < nbc; e += NT) bcache[e] = pack_hit(P.bent[b0 + e]);
+        const uint32_t ntl = (seg_len + LT - 1) >> tile_log2;  // tiles of this segment (<= kMaxSegTiles)
+        for (uint32_t e = tid; e < nbc; e += NT) {
+            const uint32_t w = pack_hit(P.bent[b0 + e]);
+            bcache[e] = w;
+            const uint32_t o = w >> 12, t1 = o >> tile_log2;
+            if (t1 < ntl) atomicAdd(&s_bcnt[t1], 1u);
+            if ((o & (LT - 1)) == 0 && t1 >= 1) atomicAdd(&s_bcnt[t1 - 1], 1u);
+        }
+        __syncthreads();
+        if (warp == 0) {  // exclusive prefix of the bin counts; the counts become write cursors
+            const uint32_t i0 = 2 * lane, i1 = 2 * lane + 1;
+            const uint32_t c0 = i0 < ntl ? s_bcnt[i0] : 0u, c1 = i1 < ntl ? s_bcnt[i1] : 0u;
+            uint32_t inc = c0 + c1;
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, inc, o);
+                if (lane >= (uint32_t)o) inc += y;
+            }
+            const uint32_t ex = inc - c0 - c1;
+            if (i0 < ntl) s_bstart[i0] = s_bcnt[i0] = ex;
+            if (i1 < ntl) s_bstart[i1] = s_bcnt[i1] = ex + c0;
+            if (lane == 31) s_bstart[ntl] = inc;
+        }
+        __syncthreads();
+        for (uint32_t e = tid; e < nbc; e += NT) {
+            const uint32_t w = bcache[e];
+            const uint32_t o = w >> 12, t1 = o >> tile_log2;
+            if (t1 < ntl) bsort[atomicAdd(&s_bcnt[t1], 1u)] = w;
+            if ((o & (LT - 1)) == 0 && t1 >= 1) bsort[atomicAdd(&s_bcnt[t1 - 1], 1u)] = w;
+        }
         const uint32_t nsparse = s_nsparse, nruns = s_nruns[warp];
         const uint32_t kinds = iv.kinds;
 
@@ -371,9 +408,9 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
                     if (x <= tl) red_add_shared(tile_s + ((x >> VSH) << 2), d.y << ((x & (VPW - 1)) * VBITS));
                 }
             }
-            for (uint32_t e = tid; e < nbc; e += NT) {
-                const uint32_t w = bcache[e];
-                const uint32_t x = (w >> 12) - t0;  // wraps to a large value below t0
+            for (uint32_t e = s_bstart[t0 >> tile_log2] + tid, e1 = s_bstart[(t0 >> tile_log2) + 1]; e < e1; e += NT) {
+                const uint32_t w = bsort[e];
+                const uint32_t x = (w >> 12) - t0;
                 if (x <= tl) {
                     const uint32_t lg7 = w & 0xfffu;
                     const uint32_t lg = VB == 4 ? lg7 << 9 : VB == 2 ? lg7 << 1 : (lg7 + 63u) >> 6;
@@ -510,8 +547,10 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
                 }
             }
         }
-        // every thread has read s_seg .. s_b1 (a barrier of the tile loop lies between)
+        // every thread has read s_seg .. s_b1 and is done with the bins (a barrier of the tile
+        // loop lies between)
         if (tid == NT - 1) fetch(nxt);
+        if (tid <= kMaxSegTiles) s_bcnt[tid] = 0;
     }
 }
 
