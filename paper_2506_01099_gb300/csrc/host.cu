@@ -56,10 +56,10 @@ static uint64_t isqrt64(uint64_t x) {
 // ----------------------------------------------------------------- tune ----
 static void tune_defaults(bnx_tune *t) {
     t->tile_log2 = 15;
-    t->seg_tiles = 8;
+    t->seg_tiles = 16;
     t->threads = 256;
     t->ctas_per_sm = 0;
-    t->small_q_log2 = 15;
+    t->small_q_log2 = 16;
     t->tile_kind = kTileLog8;
 }
 
