@@ -489,13 +489,21 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
                     const uint32_t n0 = (uint32_t)(t_lo + G * g);  // low 32 bits suffice modulo 2^M
                     // does [n0, n0 + G] hold a multiple of 2^M?
                     const bool hi2 = ((n0 + G) & (M2 - 1)) <= G;
-                    if (all_cand || logc || hi2) {
+                    if (all_cand || logc) {
 #pragma unroll
                         for (uint32_t u = 0; u < G; u++) {
                             const uint32_t nl = n0 + u;
                             const bool h = ((nl & (M2 - 1)) == 0) || (((nl + 1) & (M2 - 1)) == 0);
                             if ((all_cand || ss[u] >= T32 || h) && G * g + u < tl) cm |= 1u << u;
                         }
+                    } else if (hi2) {
+                        // about one group per tile: only the n next to the multiple n0 + u0 of 2^M
+                        // (n = n0 + u0 and n = n0 + u0 - 1), without the loop over the group
+                        const uint32_t u0 = (0u - n0) & (M2 - 1);  // <= G here
+                        if (u0 < G) cm |= 1u << u0;
+                        if (u0 >= 1) cm |= 1u << (u0 - 1);
+                        const uint32_t left = tl - G * g;  // values of the group inside the tile
+                        if (left < G) cm &= (1u << left) - 1u;
                     }
                 }
                 // candidates whose bound, with the exact power of 2 of P, still reaches the
