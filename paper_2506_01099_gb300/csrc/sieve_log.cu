@@ -249,24 +249,35 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
             s_nsparse = incw <= P.n_sched ? incw : 0u;  // n_sched always covers them
             if (incw > P.n_sched && blockIdx.x == 0) atomicOr(&P.ctr->err, kErrSchedule);
         }
-        // lane w < NT/32 lists the runs of warp w
+        // lane w < NT/32 lists the runs of warp w.  The shares are equal in estimated cost, not
+        // in rounds: a run costs about kRunSetup instructions to set up and kRoundCost per
+        // round, and the prime powers with few rounds (and so many runs) come last.  Round k of
+        // a prime power whose cost span starts at cs sits at cs + kRunSetup + (k + 1/2) kRoundCost;
+        // warp w takes the rounds that sit in [T w / NT*32, T (w+1) / NT*32).
         if (lane < nwarps) {
-            uint32_t R = 0;
+            constexpr int kRunSetup = 80, kRoundCost = 8;
+            int T = 0;
             for (uint32_t j = 0; j < nspp; j++) {
-                const uint32_t r = sdesc[j].w;
-                if (r > 1) R += r;
+                const int r = (int)sdesc[j].w;
+                if (r > 1) T += kRunSetup + r * kRoundCost;
             }
-            const uint32_t b = (uint32_t)((uint64_t)R * lane / nwarps), e = (uint32_t)((uint64_t)R * (lane + 1) / nwarps);
-            uint32_t cs = 0, nr = 0;
+            const int b = (int)((int64_t)T * lane / nwarps), e = (int)((int64_t)T * (lane + 1) / nwarps);
+            auto first_at = [&](int pos, int cs, int r) -> int {  // first round k sitting at or after pos
+                const int x = 2 * (pos - cs - kRunSetup) - kRoundCost;  // in half-units
+                const int k = x <= 0 ? 0 : (x + 2 * kRoundCost - 1) / (2 * kRoundCost);
+                return k < r ? k : r;
+            };
+            int cs = 0;
+            uint32_t nr = 0;
             for (uint32_t j = 0; j < nspp; j++) {
-                const uint32_t r = sdesc[j].w;
+                const int r = (int)sdesc[j].w;
                 if (r < 2) continue;
-                const uint32_t lo = max(b, cs), hi = min(e, cs + r);
-                if (lo < hi) {
-                    if (nr < kMaxRuns) s_runs[lane][nr] = j | ((lo - cs) << 8) | ((hi - lo) << 20);
+                const int k0 = first_at(b, cs, r), k1 = first_at(e, cs, r);
+                if (k0 < k1) {
+                    if (nr < kMaxRuns) s_runs[lane][nr] = j | ((uint32_t)k0 << 8) | ((uint32_t)(k1 - k0) << 20);
                     nr++;
                 }
-                cs += r;
+                cs += kRunSetup + r * kRoundCost;
             }
             s_nruns[lane] = nr < kMaxRuns ? nr : kMaxRuns;
             if (nr > kMaxRuns) atomicOr(&P.ctr->err, kErrSchedule);
