@@ -387,6 +387,21 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
                 }
             }
             __syncthreads();
+            // the first pass of packed slots (below) is loaded now and struck after the runs, so
+            // that its two dependent shared loads overlap the runs
+            uint32_t sa0 = 0, sv0 = 0;
+            bool sp0 = false;
+            {
+                const uint32_t sl = warp * 32 + lane;
+                if (sl < nsparse) {
+                    const uint32_t e = sched[sl];
+                    const uint4 d = sdesc[e & 255u];
+                    const uint32_t x = d.z + (e >> 8) * d.x;
+                    sp0 = x <= tl;
+                    sa0 = tile_s + ((x >> VSH) << 2);
+                    sv0 = d.y << ((x & (VPW - 1)) * VBITS);
+                }
+            }
             // this warp's runs of dense rounds
             for (uint32_t k = 0; k < nruns; k++) {
                 const uint32_t run = s_runs[warp][k];
@@ -411,7 +426,8 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
                 }
             }
             // packed slots of the single-round prime powers
-            for (uint32_t sl = warp * 32 + lane; sl < ((nsparse + 31) & ~31u); sl += NT) {
+            if (sp0) red_add_shared(sa0, sv0);
+            for (uint32_t sl = warp * 32 + lane + NT; sl < ((nsparse + 31) & ~31u); sl += NT) {
                 if (sl < nsparse) {
                     const uint32_t e = sched[sl];
                     const uint4 d = sdesc[e & 255u];
