@@ -226,6 +226,53 @@ def test_batch_family_members(ctx):
         assert mine == theorem1_pairs(lo, hi, k)
 
 
+def test_batched_workload_full_size(B, orc):
+    """The benchmark's own step at full size and in its launch configuration (the default
+    tuning): 4096 seeded intervals in [2^32, 2^40), 4.6e11 integers.  Every interval's
+    pairs are its Theorem 1 family members (the theorem is complete below 1.4e12), and
+    sampled intervals, and sampled windows of long ones, equal the oracle's."""
+    from paper_2506_01099_gb300 import workloads as W
+
+    ivs = W.batch_intervals(4096)
+    with B.Context(0, max_hi=MAX_HI) as c:
+        pairs, offs = c.batch(ivs)
+        assert len(offs) == len(ivs) + 1
+        for i, iv in enumerate(ivs):
+            mine = [(m, n, kd) for (_, m, n, kd) in pairs[offs[i]:offs[i + 1]]]
+            assert mine == theorem1_pairs(iv.lo, iv.hi, iv.kinds), i
+        rng = np.random.default_rng(11)
+        short = [i for i, iv in enumerate(ivs) if iv.hi - iv.lo <= (1 << 20)]
+        for i in rng.choice(short, 12, replace=False):
+            iv = ivs[int(i)]
+            mine = [(m, n, kd) for (_, m, n, kd) in pairs[offs[i]:offs[i + 1]]]
+            assert mine == orc.pairs_crt(iv.lo, iv.hi, iv.kinds), iv
+        # windows of long intervals searched alone with the same tuning, against the oracle
+        # (pairs and the survivor counts of the per-kind conditions)
+        long_ = [iv for iv in ivs if iv.hi - iv.lo >= (1 << 26)]
+        for k in rng.choice(len(long_), 4, replace=False):
+            iv = long_[int(k)]
+            lo = iv.lo + int(rng.integers(0, iv.hi - iv.lo - (1 << 21)))
+            assert c.search(lo, lo + (1 << 21), iv.kinds) == orc.pairs_crt(lo, lo + (1 << 21), iv.kinds)
+            st = c.stats()
+            assert (st["survivors1"], st["survivors2"]) == orc.filter_counts(lo, lo + (1 << 21), iv.kinds)
+
+
+def test_large_windows_full(ctx):
+    """The two large windows whole: [2^40, 2^40 + 2^37) holds exactly Theorem 1's
+    second-kind member (2^20 + 1, 2^40 + 2^21), [1.3e12, 1.4e12) nothing; the plain call
+    and the batch of 2^30-integer pieces agree."""
+    from paper_2506_01099_gb300 import workloads as W
+
+    for which in (0, 1):
+        lo, hi = W.LARGE_WINDOWS[which]
+        want = theorem1_pairs(lo, hi)
+        assert ctx.search(lo, hi) == want
+        pairs, _ = ctx.batch(W.large_window_intervals(which))
+        assert sorted((m, n, kd) for (_, m, n, kd) in pairs) == want
+    assert theorem1_pairs(*W.LARGE_WINDOWS[0]) == [(1048577, 1099513724928, 2)]
+    assert theorem1_pairs(*W.LARGE_WINDOWS[1]) == []
+
+
 def test_bad_arguments(B, ctx):
     for args in ((0, 10, 3), (10, 10, 3), (5, 4, 3), (1, MAX_HI + 1, 3), (1, 10, 0), (1, 10, 8)):
         with pytest.raises(B.BnxError) as e:
