@@ -17,17 +17,17 @@
 // and n is rejected when that bound falls below the tile's smallest threshold.
 // Every other n (a bound that does not reject, or n, n+1 next to a multiple of
 // 2^M) is a candidate.  A candidate whose exact power of 2 still rejects it is
-// dropped; the rest get exact square parts (exact-division tests by the in-tile
-// primes, plus the segment's bucket entries of the larger primes) and the exact
-// 128-bit conditions.
+// dropped; the rest go to a list that k_cand (below) checks with exact square
+// parts (exact-division tests by the in-tile primes, plus the segment's bucket
+// entries of the larger primes) and the exact 128-bit conditions.
 #include "bnx_internal.cuh"
 
 namespace bnx {
 
 namespace {
 
-// The first 512 bucket entries of a segment (a segment of 2^18 values near 2^40
-// holds about 280 at Q = 2^15) are cached in shared memory, each packed into one
+// The first 512 bucket entries of a segment (a segment of 2^19 values near 2^40
+// holds about 370 at Q = 2^16) are cached in shared memory, each packed into one
 // word: (offset in the segment) << 12 | lg7, lg7 = ceil(log2 p * 2^7) with
 // margin (p < 2^22: lg7 < 2^12).  Offsets reach the segment length, so the
 // cache is used for segments of at most 2^19 values; the entries of larger
@@ -135,7 +135,7 @@ __device__ __noinline__ uint32_t exact_kinds_log(uint64_t n, uint64_t s0, uint64
 }
 
 // CTAs per SM the register allocation must allow: 64 registers per thread, or for the
-// u8 tile (about 37 KB of shared memory per CTA at 2^15 values) 5 CTAs of 256 threads
+// u8 tile (about 44 KB of shared memory per CTA at 2^15 values) 5 CTAs of 256 threads
 // (46 registers, no spills), which measured 2% faster than 4.
 template <int NT, int VB>
 struct LogMinBlocks {
