@@ -419,10 +419,12 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
                     uint32_t a = tile_s + ((x >> VSH) << 2);
                     const uint32_t alim = tile_s + (((xl - ((xl - x) & (VPW - 1))) >> VSH) << 2);
                     const uint32_t bstep = ((32 >> VSH) * q) << 2;
-#pragma unroll 4
-                    for (uint32_t r = 0; r < reps; r++, a += bstep) {
-                        if (a <= alim) red_add_shared(a, lg);
+                    // rounds bounded by the lane's last address alone (no trip count), two per step
+                    for (; a + bstep <= alim; a += 2 * bstep) {
+                        red_add_shared(a, lg);
+                        red_add_shared(a + bstep, lg);
                     }
+                    if (a <= alim) red_add_shared(a, lg);
                 }
             }
             // packed slots of the single-round prime powers
