@@ -36,7 +36,8 @@ MAX_HI = (1 << 41) + (1 << 31)
 TUNE_CACHE = os.path.join(ROOT, "paper_2506_01099_gb300", "tune_cache.json")
 KERNELS_PER_STEP = 11  # plan, bucket count, 3 scan kernels, bucket fill, sieve, exact check, verify, sort, offsets
 # Algorithmic integer lane-operations per searched integer of each tile kind (the method as
-# built).  Strikes: sum over odd prime powers q = p^k, k >= 2, of 1/q
+# built; the ALU roofline divides them by 152 SMs x 128 lanes x the maximum SM clock).
+# Strikes: sum over odd prime powers q = p^k, k >= 2, of 1/q
 # = sum_{p>=3} 1/(p(p-1)) = 0.2732 per integer, each an address step, a bound test and a
 # shared-memory reduction (3 ops).  Log tiles: the pair test of a word of VPW values is a
 # funnel shift, the pair add, the threshold add and the flag OR (4 ops per word), plus a

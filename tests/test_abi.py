@@ -23,7 +23,7 @@ def lib():
     return B.lib()
 
 
-def test_header_declares_the_survey_boundary():
+def test_header_declares_the_boundary_calls():
     names = declared()
     for n in ("bnx_create", "bnx_destroy", "bnx_search", "bnx_rad_segment", "bnx_search_hash", "bnx_batch",
               "bnx_server_submit", "bnx_server_poll", "bnx_strerror", "bnx_autotune"):
