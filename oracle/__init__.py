@@ -53,7 +53,7 @@ class Oracle:
         lib.orc_nprimes_upto.argtypes, lib.orc_nprimes_upto.restype = [u64], u64
         lib.orc_rad_sieve.argtypes = [u64, u64, ctypes.POINTER(u64)]
         lib.orc_rad_sieve.restype = i32
-        for f in ("orc_pairs_brute", "orc_pairs_sort"):
+        for f in ("orc_pairs_brute", "orc_pairs_sort", "orc_pairs_map"):
             getattr(lib, f).argtypes = [u64, u32, ctypes.POINTER(OrcPair), sz]
             getattr(lib, f).restype = sz
         lib.orc_pairs_crt.argtypes = [u64, u64, u32, ctypes.POINTER(OrcPair), sz, i32]
@@ -109,6 +109,10 @@ class Oracle:
     def pairs_sort(self, S: int, kinds: int = 3):
         """All pairs with m < n < S (S <= 2^26), by Algorithm 2 with group-wise pairing."""
         return self._collect(self.lib.orc_pairs_sort, S, kinds)
+
+    def pairs_map(self, S: int, kinds: int = 3):
+        """All pairs with m < n < S (S <= 2^26), by a hash table of the 2-sets (Algorithm 3's collision search)."""
+        return self._collect(self.lib.orc_pairs_map, S, kinds)
 
     def pairs_crt(self, lo: int, hi: int, kinds: int = 3, nthreads: int = 0):
         """All pairs with lo <= n < hi and any m < n, by CRT candidate enumeration."""

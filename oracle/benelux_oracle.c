@@ -26,6 +26,9 @@
  *   orc_pairs_sort   Algorithm 2 (sort the 2-sets {rad n, rad n+1}); every pair
  *                    inside a group of equal sets is reported, not only adjacent
  *                    entries (a group can hold three integers: {2,3} for 2, 3, 8)
+ *   orc_pairs_map    the same 2-sets collected in a hash table of key -> list of n
+ *                    (the collision search of Algorithm 3, Sec. 2.2, over one
+ *                    range), an independent route to orc_pairs_sort's result
  *   orc_pairs_crt    the candidate enumeration that the Chinese remainder theorem
  *                    forces on any pair (derived below); candidates are verified
  *                    with orc_rad_td, never with the gcd shortcut of the GPU path
@@ -299,6 +302,54 @@ size_t orc_pairs_sort(uint64_t S, uint32_t kinds, orc_pair *out, size_t cap) {
     free(r);
     free(list);
     if (cnt && cnt <= cap) qsort(out, cnt, sizeof(orc_pair), cmp_pair);
+    return cnt;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Key search by a hash table (Algorithm 3's collision detection, Sec. 2.2)    */
+/* ------------------------------------------------------------------------ */
+
+/* Open addressing, linear probing; a slot holds a key {k1 < k2} and the last n
+ * inserted with it, and nxt[n] links the earlier n of the same key.  Every n
+ * pairs with every earlier n of its key. */
+size_t orc_pairs_map(uint64_t S, uint32_t kinds, orc_pair *out, size_t cap) {
+    if (S < 2 || S > (1u << 26)) return 0;
+    uint64_t slots = 1;
+    while (slots < 2 * S) slots <<= 1;
+    uint64_t *r = (uint64_t *)malloc((S + 1) * sizeof(uint64_t));
+    uint64_t *key1 = (uint64_t *)calloc(slots, sizeof(uint64_t));
+    uint64_t *key2 = (uint64_t *)calloc(slots, sizeof(uint64_t));
+    uint64_t *last = (uint64_t *)calloc(slots, sizeof(uint64_t)); /* 0 = empty slot */
+    uint64_t *nxt = (uint64_t *)calloc(S + 1, sizeof(uint64_t));
+    size_t cnt = 0;
+    if (!r || !key1 || !key2 || !last || !nxt) goto done;
+    orc_rad_sieve(1, S, r + 1);
+    for (uint64_t n = 1; n < S; n++) {
+        const uint64_t u = r[n], v = r[n + 1];
+        const uint64_t k1 = u < v ? u : v, k2 = u < v ? v : u;
+        uint64_t h = (k1 * 0x9e3779b97f4a7c15ull) ^ (k2 * 0xc2b2ae3d27d4eb4full);
+        h ^= h >> 29;
+        uint64_t i = h & (slots - 1);
+        while (last[i] && !(key1[i] == k1 && key2[i] == k2)) i = (i + 1) & (slots - 1);
+        if (last[i]) {
+            for (uint64_t m = last[i]; m; m = nxt[m]) {
+                const uint32_t kind = (r[m] == r[n]) ? 1 : 2;
+                if (kinds & kind) push_pair(out, cap, &cnt, m, n, kind);
+            }
+        } else {
+            key1[i] = k1;
+            key2[i] = k2;
+        }
+        nxt[n] = last[i];
+        last[i] = n;
+    }
+    if (cnt && cnt <= cap) qsort(out, cnt, sizeof(orc_pair), cmp_pair);
+done:
+    free(r);
+    free(key1);
+    free(key2);
+    free(last);
+    free(nxt);
     return cnt;
 }
 

@@ -137,6 +137,17 @@ def test_sort_equals_crt(orc):
     assert orc.pairs_sort(1 << 22) == orc.pairs_crt(1, 1 << 22)
 
 
+def test_hash_map_search(orc):
+    """The hash-table key search finds Theorem 1's pairs below 2^20 and agrees with the
+    sort-based search and the CRT enumeration on [1, 2^22), per kind."""
+    assert orc.pairs_map(1 << 20) == theorem1_pairs(1, 1 << 20)
+    for kinds in (1, 2, 3):
+        got = orc.pairs_map(1 << 22, kinds)
+        assert got == orc.pairs_sort(1 << 22, kinds) == orc.pairs_crt(1, 1 << 22, kinds)
+    # a group of three equal keys ({2, 3} is the key of 2, 3 and 8): every pair, not only neighbours
+    assert orc.pairs_map(9) == [(2, 3, 2), (2, 8, 1), (3, 8, 2)]
+
+
 def test_crt_window_at_2p40(orc):
     """[2^40, 2^40 + 2^30) holds exactly one pair, of the second kind."""
     lo = 2**40
