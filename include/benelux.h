@@ -228,7 +228,9 @@ int bnx_batch(bnx_ctx *ctx, const bnx_interval *iv, size_t k, bnx_pair *out, siz
 typedef struct {
     uint32_t max_active;      /* requests on the device at once (slots) */
     uint32_t pad;
-    uint64_t slice;           /* integers of each active request per iteration */
+    uint64_t slice;           /* integers of each active request per iteration: at least
+                                 slice, and an equal share of slice * max_active when
+                                 fewer than max_active requests are active */
     uint64_t mem_budget;      /* bytes of workspace admission may commit (0: 90% of free HBM) */
 } bnx_server_cfg;
 

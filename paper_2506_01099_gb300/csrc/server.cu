@@ -5,7 +5,10 @@
 //      next slice needs fits the memory budget (free HBM by default);
 //   2. cuts the next slice of every active request and runs all slices as one
 //      batched pipeline (one persistent sieve launch over the shared queue), so
-//      the work of requests that arrived at different times overlaps on the GPU;
+//      the work of requests that arrived at different times overlaps on the GPU.
+//      An iteration covers up to slice * max_active integers, shared equally by the
+//      active requests (at least `slice` each): a request that runs alone or with
+//      few others advances in long slices, and with a full set each gets `slice`;
 //   3. appends each slice's pairs to its request and retires finished requests.
 // Results are exact, so a request's pairs are the same alone and in any mix.
 #include <algorithm>
@@ -83,6 +86,9 @@ static void serve(bnx_ctx *c) {
             batch = S.active;
         }
         const size_t k = batch.size();
+        // this iteration's slice: an equal share of slice * max_active, at least `slice`
+        const uint64_t budget = S.cfg.slice > UINT64_MAX / S.cfg.max_active ? UINT64_MAX : S.cfg.slice * S.cfg.max_active;
+        const uint64_t per = std::max<uint64_t>(S.cfg.slice, budget / k);
         PlanTotals t0{0, 0, 0, 0};
         int rc = ensure_ws(c, t0, k);
         if (rc == BNX_OK) {
@@ -91,7 +97,7 @@ static void serve(bnx_ctx *c) {
                 IvDev &d = c->h_ivs[i];
                 memset(&d, 0, sizeof d);
                 d.lo = r.cursor;
-                d.hi = std::min(r.iv.hi, r.cursor + S.cfg.slice);
+                d.hi = std::min(r.iv.hi, r.cursor + per);
                 d.kinds = r.iv.kinds;
                 d.id = (uint32_t)i;
             }
@@ -113,7 +119,7 @@ static void serve(bnx_ctx *c) {
                     p.iv = r.iv.id;
                     r.pairs.push_back(p);
                 }
-                r.cursor = std::min(r.iv.hi, r.cursor + S.cfg.slice);
+                r.cursor = std::min(r.iv.hi, r.cursor + per);
             } else {
                 r.status = rc;
                 r.cursor = r.iv.hi;
