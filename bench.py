@@ -115,11 +115,24 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def code_sha256(path: str) -> str:
+    """sha256 of a CUDA source without its // comments and blank lines, so that a record
+    of counters stays valid across comment edits and is dropped by any change of code."""
+    import hashlib
+    import re
+
+    lines = []
+    for ln in open(path, encoding="utf-8").read().splitlines():
+        ln = re.sub(r"//.*$", "", ln).rstrip()
+        if ln.strip():
+            lines.append(ln)
+    return hashlib.sha256("\n".join(lines).encode()).hexdigest()
+
+
 def sieve_record(tile_kind: int):
     """The committed ncu record (DRAM bytes and warp instructions per integer) of the sieve
-    with this tile kind -- or None once the kernel source differs from the one it measured."""
+    with this tile kind -- or None once the kernel's code differs from the one it measured."""
     import glob
-    import hashlib
 
     rec = None
     for f in glob.glob(os.path.join(ROOT, "profiles", "k_sieve_log_*_traffic.json")):
@@ -132,10 +145,10 @@ def sieve_record(tile_kind: int):
     if rec is None:
         return None
     try:
-        src = open(os.path.join(ROOT, rec["source"]), "rb").read()
+        h = code_sha256(os.path.join(ROOT, rec["source"]))
     except Exception:
         return None
-    if hashlib.sha256(src).hexdigest() != rec["source_sha256"]:
+    if h != rec.get("code_sha256"):
         return None
     return rec
 

@@ -220,9 +220,10 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
     __syncthreads();
     // Static strike schedule, built once per launch.
     //  - Dense prime powers (at least two rounds of 32 multiples per tile): their rounds, in
-    //    order of j, are cut into NT/32 contiguous shares of equal length, one per warp.  A
-    //    warp's share is a list of runs (j, first round, rounds), each struck as consecutive
-    //    rounds of 32 multiples, so a warp sets up each prime power it touches once per tile.
+    //    order of j, are cut into NT/32 contiguous shares of equal estimated cost (below), one
+    //    per warp.  A warp's share is a list of runs (j, first round, rounds), each struck as
+    //    consecutive rounds of 32 multiples, so a warp sets up each prime power it touches
+    //    once per tile.
     //  - Single-round prime powers (at most 32 multiples per tile): one slot (j, m) per
     //    possible multiple m, packed 32 to a warp pass in `sched`, so that a warp pass is not
     //    spent on a handful of strikes.
