@@ -90,3 +90,21 @@ def test_product_never_imports_the_oracle():
                 text = open(os.path.join(dirpath, f)).read()
                 assert not re.search(r"^\s*(import|from)\s+oracle\b", text, re.M), f
                 assert "benelux_oracle" not in text and "liboracle" not in text, f
+
+
+def test_ncu_record_follows_the_code_not_the_comments(tmp_path):
+    """The benchmark keys its committed ncu record (traffic, instructions per integer) by a
+    hash of the sieve's code: comments and blank lines do not change it, code does."""
+    import sys
+
+    sys.path.insert(0, ROOT)
+    import bench
+
+    src = tmp_path / "k.cu"
+    src.write_text("int f(int x) {\n    return x + 1;  // one more\n}\n")
+    h = bench.code_sha256(str(src))
+    src.write_text("// a kernel\nint f(int x) {\n\n    return x + 1;  // the successor\n}\n")
+    assert bench.code_sha256(str(src)) == h
+    src.write_text("int f(int x) {\n    return x + 2;\n}\n")
+    assert bench.code_sha256(str(src)) != h
+    assert bench.sieve_record(3) is not None  # the committed capture matches the current kernel
