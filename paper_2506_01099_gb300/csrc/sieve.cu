@@ -115,13 +115,27 @@ __device__ __forceinline__ uint64_t fast_mod(uint64_t v, uint64_t q, uint64_t m)
     return r >= q ? r - q : r;
 }
 
+// gcur (fill only): the write cursors are the global per-segment counters (zeroed after
+// the count), for launches in which several blocks share a chunk
 template <bool FILL>
 __device__ __forceinline__ void bucket_hit(const Plan &P, const IvDev &iv, uint64_t y, uint32_t p, uint64_t nseg,
-                                           uint64_t s_first, uint32_t *hist, const unsigned long long *sbase) {
+                                           uint64_t s_first, uint32_t *hist, const unsigned long long *sbase,
+                                           bool gcur) {
     const uint64_t lseg = 1ull << P.seg_log2;
     const uint64_t d = y - iv.lo;
     const uint64_t s = d >> P.seg_log2;
     const uint32_t o = (uint32_t)(d & (lseg - 1));
+    if (FILL && gcur) {
+        if (s < nseg) {
+            const uint64_t seg = iv.seg_base + s;
+            P.bent[P.boff[seg] + atomicAdd(&P.bcnt[seg], 1u)] = make_uint2(o, p);
+        }
+        if (o == 0 && s > 0) {  // the previous segment's halo value
+            const uint64_t seg = iv.seg_base + s - 1;
+            P.bent[P.boff[seg] + atomicAdd(&P.bcnt[seg], 1u)] = make_uint2((uint32_t)lseg, p);
+        }
+        return;
+    }
     if (s < nseg) {
         const uint32_t l = (uint32_t)(s - s_first);
         const uint32_t pos = atomicAdd(&hist[l], 1u);
@@ -153,7 +167,15 @@ __global__ void __launch_bounds__(256) k_bucket(Plan P) {
         if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&P.ctr->err, kErrBucketOverflow);
         return;
     }
-    for (uint64_t c = blockIdx.x; c < total_chunks; c += gridDim.x) {
+    if (total_chunks == 0) return;
+    // A launch with few chunks (a single short search) shares each chunk among `parts`
+    // blocks, each taking every parts-th prime power; the fill then writes through global
+    // cursors.  With more chunks a block owns a chunk, with its cursors in shared memory.
+    const uint32_t parts = total_chunks <= 8 ? max(1u, gridDim.x / (uint32_t)total_chunks) : 1u;
+    const bool gcur = parts > 1;
+    for (uint64_t item = blockIdx.x; item < total_chunks * parts; item += gridDim.x) {
+        const uint64_t c = item / parts;
+        const uint32_t part = (uint32_t)(item % parts);
         if (threadIdx.x == 0) s_iv = find_iv<false>(P.ivs, k, c);
         __syncthreads();
         const IvDev iv = P.ivs[s_iv];
@@ -166,25 +188,25 @@ __global__ void __launch_bounds__(256) k_bucket(Plan P) {
         const uint32_t nsc = (uint32_t)(nseg - s_first < kChunkSegs ? nseg - s_first : kChunkSegs);
         for (uint32_t i = threadIdx.x; i < kChunkSegs; i += blockDim.x) {
             hist[i] = 0;
-            if (FILL && i < nsc) sbase[i] = P.boff[iv.seg_base + s_first + i];
-            if (!FILL && i < nsc) P.seg_iv[iv.seg_base + s_first + i] = s_iv;  // for the sieve's queue
+            if (FILL && !gcur && i < nsc) sbase[i] = P.boff[iv.seg_base + s_first + i];
+            if (!FILL && part == 0 && i < nsc) P.seg_iv[iv.seg_base + s_first + i] = s_iv;  // for the sieve's queue
         }
         __syncthreads();
         // dense prime powers: a warp per q, lanes on consecutive multiples
-        for (uint32_t j = warp; j < P.n_lpp_dense; j += nwarps) {
+        for (uint32_t j = part * nwarps + warp; j < P.n_lpp_dense; j += nwarps * parts) {
             const LargePP e = P.lpp[j];
             if (e.q > v1) break;
             const uint64_t r = fast_mod(v0, e.q, e.m);
             for (uint64_t y = (r ? v0 + (e.q - r) : v0) + lane * e.q; y <= v1; y += 32 * e.q)
-                bucket_hit<FILL>(P, iv, y, e.p, nseg, s_first, hist, sbase);
+                bucket_hit<FILL>(P, iv, y, e.p, nseg, s_first, hist, sbase, gcur);
         }
         // sparse prime powers: a thread per q
-        for (uint32_t j = P.n_lpp_dense + threadIdx.x; j < P.n_lpp; j += blockDim.x) {
+        for (uint32_t j = P.n_lpp_dense + part * blockDim.x + threadIdx.x; j < P.n_lpp; j += blockDim.x * parts) {
             const LargePP e = P.lpp[j];
             if (e.q > v1) break;
             const uint64_t r = fast_mod(v0, e.q, e.m);
             for (uint64_t y = r ? v0 + (e.q - r) : v0; y <= v1; y += e.q)
-                bucket_hit<FILL>(P, iv, y, e.p, nseg, s_first, hist, sbase);
+                bucket_hit<FILL>(P, iv, y, e.p, nseg, s_first, hist, sbase, gcur);
         }
         __syncthreads();
         if (!FILL)
