@@ -221,3 +221,44 @@ def test_three_term_question(orc):
     # bit 4 adds nothing to bit 1, and the brute force agrees with the CRT path
     assert orc.pairs_crt(1, 1 << 22, 5) == theorem1_pairs(1, 1 << 22, 1)
     assert orc.pairs_brute(1 << 12, 7) == theorem1_pairs(1, 1 << 12, 3)
+
+
+def _rad_sympy(x: int) -> int:
+    from sympy import primefactors
+
+    r = 1
+    for p in primefactors(x):
+        r *= p
+    return r
+
+
+def _conditions_brute(lo: int, hi: int):
+    """The per-kind necessary conditions counted from their definitions, with radicals
+    from sympy: first kind rad(n) rad(n+1) <= n - 1; second kind some multiple of
+    rad(n) rad(n+1) in [n + 2, 2n]."""
+    c1 = c2 = 0
+    rads = {x: _rad_sympy(x) for x in range(lo, hi + 1)}
+    for n in range(lo, hi):
+        ab = rads[n] * rads[n + 1]
+        if ab <= n - 1:
+            c1 += 1
+        if ab <= 2 * n and -(-(n + 2) // ab) <= (2 * n) // ab:
+            c2 += 1
+    return c1, c2
+
+
+def test_filter_counts_brute_force(orc):
+    """orc_filter_counts equals the conditions evaluated one by one (brute force, sympy
+    radicals) on [1, 2^14) and on a window at 2^40."""
+    pytest.importorskip("sympy")
+    assert orc.filter_counts(1, 1 << 14) == _conditions_brute(1, 1 << 14)
+    lo = (1 << 40) - 300
+    assert orc.filter_counts(lo, lo + 1024) == _conditions_brute(lo, lo + 1024)
+
+
+def test_hash_keys_brute_force(orc):
+    """orc_hash_keys(S) is the number of x in [1, S) with rad(x) rad(x+1) <= 2S (brute force)."""
+    pytest.importorskip("sympy")
+    for S in (2, 3, 100, 1 << 13):
+        want = sum(1 for x in range(1, S) if _rad_sympy(x) * _rad_sympy(x + 1) <= 2 * S)
+        assert orc.hash_keys(S) == want, S
