@@ -262,7 +262,8 @@ def cpu_full_ranges():
 # ---------------------------------------------------------------------------
 
 def run_reference(args):
-    ws, rank, _ = dist_init()
+    # no collective: under torchrun only rank 0 works and prints, the other ranks exit at once
+    rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return 0
     ivs = W.batch_intervals(4096)
