@@ -225,18 +225,27 @@ def oracle_sample(intervals, budget_integers: int):
     return out, tot
 
 
+def host_cores() -> int:
+    """Cores this process may run on (torchrun sets OMP_NUM_THREADS=1, so the oracle is
+    given this thread count explicitly)."""
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
 def cpu_baseline(intervals, budget_integers: int):
     import oracle
 
     orc = oracle.load()
     sample, tot = oracle_sample(intervals, budget_integers)
     orc.lib.orc_init(2 * max(iv.hi for iv in sample) + 2)
+    cores = host_cores()
     t0 = time.perf_counter()
     npairs = 0
     for iv in sample:
-        npairs += len(orc.pairs_crt(iv.lo, iv.hi, iv.kinds))
+        npairs += len(orc.pairs_crt(iv.lo, iv.hi, iv.kinds, nthreads=cores))
     dt = time.perf_counter() - t0
-    cores = os.cpu_count() or 1
     return {"value": tot / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
             "sample": f"first {tot} integers of the batched workload ({len(sample)} leading interval pieces), "
                       f"{dt:.1f} s, CRT enumeration over Algorithm 1 radicals, OpenMP over 2^20-integer chunks",
@@ -249,11 +258,12 @@ def cpu_full_ranges():
     import oracle
 
     orc = oracle.load()
-    out = {"cores": os.cpu_count() or 1}
+    cores = host_cores()
+    out = {"cores": cores}
     for name, S in (("n_below_2p24", 1 << 24), ("n_below_2p32", 1 << 32)):
         orc.lib.orc_init(2 * S + 2)
         t0 = time.perf_counter()
-        pairs = orc.pairs_crt(1, S, 3)
+        pairs = orc.pairs_crt(1, S, 3, nthreads=cores)
         out[name] = {"seconds": time.perf_counter() - t0, "pairs": len(pairs),
                      "method": "CRT enumeration over Algorithm 1 radicals (orc_pairs_crt)"}
     return out
@@ -282,7 +292,7 @@ def run_reference(args):
             "config": {"workload": "batched: 4096 intervals, len log-uniform [2^16, 2^30], lo uniform [2^32, 2^40), "
                                    "kind 1|2 (seeded splitmix64); each step a bounded leading sample",
                        "sample_integers": budget},
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": host_cores(), "kind": "oracle",
                              "sample": f"first {budget} integers of the batched workload per step"},
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
