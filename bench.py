@@ -36,7 +36,7 @@ MAX_HI = (1 << 41) + (1 << 31)
 TUNE_CACHE = os.path.join(ROOT, "paper_2506_01099_gb300", "tune_cache.json")
 KERNELS_PER_STEP = 11  # plan, bucket count, 3 scan kernels, bucket fill, sieve, exact check, verify, sort, offsets
 # Algorithmic integer lane-operations per searched integer of each tile kind (the method as
-# built; the ALU roofline divides them by 152 SMs x 128 lanes x the maximum SM clock).
+# built; the ALU roofline divides them by the device's SM count x 128 lanes x the maximum SM clock).
 # Strikes: sum over odd prime powers q = p^k, k >= 2, of 1/q
 # = sum_{p>=3} 1/(p(p-1)) = 0.2732 per integer, each an address step, a bound test and a
 # shared-memory reduction (3 ops).  Log tiles: the pair test of a word of VPW values is a
@@ -48,7 +48,7 @@ ALG_OPS_PER_INT = {3: STRIKE_OPS + 4 / 4 + 2 / 16,     # u8: 4 values per word, 
                    2: STRIKE_OPS + 4 / 2 + 2 / 8,      # u16
                    0: STRIKE_OPS + 4 / 1 + 2 / 4,      # u32
                    1: 1 + 0.2732 * 5 + 2 + 10}         # exact u64 tile
-SMS, LANES_PER_CLK, SCHEDULERS, SM_MAX_MHZ = 152, 128, 4, 2070.0
+LANES_PER_CLK, SCHEDULERS, SM_MAX_MHZ = 128, 4, 2070.0  # per SM: 4 schedulers x 32 lanes
 
 
 def peaks():
@@ -401,7 +401,8 @@ def run_ours(args):
         ms_sieve = statistics.mean(sieve_ms)
         sieve_rate = integers / (ms_sieve / 1e3)
         fmax = float(pk.get("sm_max_mhz", SM_MAX_MHZ))
-        alu_peak = SMS * LANES_PER_CLK * fmax * 1e6 / 1e12
+        sms = torch.cuda.get_device_properties(local).multi_processor_count  # queried, not assumed
+        alu_peak = sms * LANES_PER_CLK * fmax * 1e6 / 1e12
         tk = ctx.tune()["tile_kind"]
         achieved = sieve_rate * ALG_OPS_PER_INT[tk] / 1e12
         rec = sieve_record(tk)
@@ -409,8 +410,8 @@ def run_ours(args):
         if rec is not None and rec.get("warp_inst_per_integer"):
             # measured warp instructions of the kernel (ncu) per integer, against the issue limit
             wipi = rec["warp_inst_per_integer"]
-            issue = {"warp_inst_per_integer": wipi, "frac": sieve_rate * wipi / (SMS * SCHEDULERS * fmax * 1e6),
-                     "note": "measured warp instructions x integers/s / (152 SMs x 4 schedulers x max clock)"}
+            issue = {"warp_inst_per_integer": wipi, "frac": sieve_rate * wipi / (sms * SCHEDULERS * fmax * 1e6),
+                     "note": f"measured warp instructions x integers/s / ({sms} SMs x 4 schedulers x max clock)"}
         cpu = None
         if not args.no_cpu and ws == 1:
             cpu = cpu_baseline(W.batch_intervals(4096), int(args.cpu_budget))
@@ -435,7 +436,9 @@ def run_ours(args):
                                     2: "k_sieve_log<search, u16 tile>",
                                     3: "k_sieve_log<search, u8 tile>"}[ctx.tune()["tile_kind"]]
                                    + " (persistent shared-memory tile sieve, fused filter + warp-ballot compaction)",
-                         "peak_source": "152 SMs x 128 lanes/clk x max SM clock (issue roofline)",
+                         "peak_source": f"{sms} SMs (queried) x 128 lanes/clk x {fmax:.0f} MHz max SM clock "
+                                        f"({pk_src}) (issue roofline)",
+                         "sms": sms,
                          "alg_ops_per_integer": ALG_OPS_PER_INT[tk], "sieve_ms_per_launch": ms_sieve,
                          "issue": issue,
                          "hbm_equivalent": {"achieved_gbs": sieve_rate * 8 / 1e9, "peak_gbs": pk["hbm_gbs"],
@@ -556,7 +559,10 @@ def merged_tune(gpu_name: str, override: str | None) -> str | None:
     return json.dumps(base) if base else None
 
 
-def profile_case(override: str | None = None):
+def profile_case(override: str | None = None, len_log2: int = 28):
+    """One warm-up search and one search of [2^40, 2^40 + 2^len_log2): a single sieve
+    launch over a window of the batched workload's magnitude (the small case for ncu;
+    len_log2 = 32 gives a launch of about a millisecond, long enough for steady state)."""
     import torch
 
     from paper_2506_01099_gb300 import benelux as B
@@ -564,8 +570,8 @@ def profile_case(override: str | None = None):
     ctx = B.Context(0, max_hi=MAX_HI, tune_json=merged_tune(torch.cuda.get_device_name(0), override))
     lo = 1 << 40
     ctx.search(lo, lo + (1 << 20))
-    pairs = ctx.search(lo, lo + (1 << 28))
-    print(json.dumps({"profile_case": [lo, lo + (1 << 28)], "pairs": pairs, "stats": ctx.stats()}))
+    pairs = ctx.search(lo, lo + (1 << len_log2))
+    print(json.dumps({"profile_case": [lo, lo + (1 << len_log2)], "pairs": pairs, "stats": ctx.stats()}))
     ctx.close()
     return 0
 
@@ -598,14 +604,16 @@ def main():
     ap.add_argument("--serve-timeout", type=float, default=120.0)
     ap.add_argument("--tune", default=None, help="JSON of bnx_tune fields applied over the cached tuning")
     ap.add_argument("--profile-case", action="store_true",
-                    help="one warm-up and one search of [2^40, 2^40 + 2^28) (small case for ncu), then exit")
+                    help="one warm-up and one search of [2^40, 2^40 + 2^LEN) (small case for ncu), then exit")
+    ap.add_argument("--profile-len-log2", type=int, default=28, metavar="LEN",
+                    help="window length of --profile-case as a power of two (default 28)")
     ap.add_argument("--profile-sorted", type=int, default=0, metavar="LG",
                     help="one Algorithm 2 search of all n < 2^LG (small case for ncu), then exit")
     args = ap.parse_args()
     if args.profile_sorted:
         return profile_sorted(args.profile_sorted)
     if args.profile_case:
-        return profile_case(args.tune)
+        return profile_case(args.tune, args.profile_len_log2)
     if args.impl == "reference":
         return run_reference(args)
     return run_ours(args)

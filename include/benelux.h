@@ -116,6 +116,15 @@ int bnx_create(bnx_ctx **out, int device, uint64_t max_hi, const char *tune_json
 /* Free every device and host resource of the context (NULL is accepted). */
 void bnx_destroy(bnx_ctx *ctx);
 
+/* Parse a tuning JSON object (the form bnx_create takes and bnx_autotune
+ * writes) into *out: the built-in defaults, overridden by the object's fields.
+ * The object is flat; its keys are bnx_tune's field names with non-negative
+ * integer values, plus "ms" (any number, ignored).  Unknown or repeated keys,
+ * non-integers, values beyond 32 bits, values outside the ranges bnx_tune
+ * states, and text after the object give BNX_E_ARG (and leave *out as it
+ * was).  Host code only; bnx_create applies the same reader. */
+int bnx_tune_parse(const char *json, bnx_tune *out);
+
 /* Read or replace the tuning of a context (replacing frees cached graphs). */
 int bnx_get_tune(const bnx_ctx *ctx, bnx_tune *out);
 int bnx_set_tune(bnx_ctx *ctx, const bnx_tune *tune);
@@ -133,11 +142,30 @@ int bnx_prime_count(const bnx_ctx *ctx, uint64_t *out);
 /* Radicals of x in [lo, lo+len): rad_out[i] = rad(lo+i) and, when sq_out is not
  * NULL, sq_out[i] = (lo+i) / rad(lo+i), the product of p^(e-1) over p^e || x.
  * This is the output of Algorithm 1 (Sec. 2.1), computed by the same
- * shared-memory tile sieve as the search.  rad_out and sq_out are DEVICE
- * pointers (uint64_t, len elements, 8-byte aligned); the call is asynchronous
- * on `stream` (NULL: the context's stream).  1 <= lo, lo + len <= max_hi,
- * 1 <= len <= 2^31.  Errors: BNX_E_ARG, BNX_E_CUDA. */
+ * shared-memory tile sieve as the search.  rad_out and sq_out (uint64_t, len
+ * elements, 8-byte aligned) are both DEVICE pointers or both HOST pointers:
+ *  - device buffers: the call is asynchronous on `stream` (NULL: the
+ *    context's stream);
+ *  - host buffers (pageable or pinned): the values are sieved into a device
+ *    staging buffer owned by the context (kept up to 256 MiB, freed after the
+ *    call above that), copied back on `stream`, and the call returns once they
+ *    are written.
+ * 1 <= lo, lo + len <= max_hi, 1 <= len <= 2^31.
+ * Errors: BNX_E_ARG, BNX_E_NOMEM, BNX_E_CUDA. */
 int bnx_rad_segment(bnx_ctx *ctx, uint64_t lo, uint64_t len, uint64_t *rad_out, uint64_t *sq_out, void *stream);
+
+/* Segment-level search: all pairs (m, n) of the requested kinds with
+ * lo <= n < lo + len and any m < n -- the output Algorithm 3 (Sec. 2.2) gives
+ * for one chunk C_i, for a caller that drives its own loop over segments (the
+ * paper's host passes only the chunk number down, Sec. 3.1).  The same staged
+ * pipeline as bnx_search (sieve, per-kind CRT conditions, compaction,
+ * verification) over the one segment; a segment's pairs do not depend on any
+ * other segment, so consecutive segments concatenate to bnx_search's result.
+ * `out` is a HOST buffer of `cap` pairs sorted by (n, m, kind).  Blocking.
+ * 1 <= len < 2^32, 1 <= lo, lo + len <= max_hi.
+ * Errors: BNX_E_ARG, BNX_E_TRUNCATED, BNX_E_NOMEM, BNX_E_CUDA, BNX_E_OVERFLOW. */
+int bnx_search_segment(bnx_ctx *ctx, uint64_t lo, uint32_t len, uint32_t kinds, bnx_pair *out, size_t cap,
+                       size_t *n_out);
 
 /* Radicals of [lo, lo+len) without allocating any device memory -- for
  * callers that cannot call cudaMalloc (their device memory is owned by another
@@ -153,6 +181,10 @@ int bnx_rad_segment(bnx_ctx *ctx, uint64_t lo, uint64_t len, uint64_t *rad_out, 
  *    anything larger is rejected with BNX_E_ARG.
  *  - The first call on a device looks up the scratch's device address
  *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *    The address is then kept per device ordinal for the life of the process,
+ *    so it belongs to the device's primary context: do not use this entry
+ *    point after cudaDeviceReset on that device, or with another CUDA context
+ *    current on it.
  *  - Every call uses the same scratch: calls that may overlap on the GPU
  *    (different streams, or threads without ordering) race.  Each call
  *    re-initialises the scratch it reads, so back-to-back calls are independent.
@@ -161,6 +193,30 @@ int bnx_rad_segment(bnx_ctx *ctx, uint64_t lo, uint64_t len, uint64_t *rad_out, 
 #define BNX_NOALLOC_MAX_HI ((uint64_t)1 << 40)
 #define BNX_NOALLOC_SCRATCH_BYTES 3145984u
 int bnx_rad_segment_noalloc(uint64_t lo, uint64_t len, uint64_t *rad_out, uint64_t *sq_out, void *stream);
+
+/* ------------------------------------------------------------------------ */
+/* Log weights of the filter                                                  */
+/* ------------------------------------------------------------------------ */
+
+/* The log-domain tiles bound the odd square part s of rad's complement x/rad(x)
+ * (Algorithm 1, Sec. 2.1, records the same prime-power hits) from above by a
+ * sum of per-prime weights, and reject n when the bound cannot meet the
+ * per-kind necessary condition.  That is exact only if every weight is at
+ * least F log2 p, F the tile's units per bit.  bnx_log_weight(p, f) is the
+ * smallest integer L with 2^L > p^(2^f) -- the bit length of p^(2^f) --
+ * computed in integers by repeated squaring with upward rounding; it never
+ * falls below the bit length and equals it unless a rounding tie intervenes.
+ * Host code only (no GPU needed); 2 <= p < 2^32, f <= 16, else 0. */
+uint32_t bnx_log_weight(uint64_t p, uint32_t frac_log2);
+
+/* For every prime p <= sqrt(max_hi) of the context's device table (ascending),
+ * the weights the log tile `tile_kind` (0 = u32, 2 = u16, 3 = u8) adds, read
+ * along the kernels' own code paths on the device: out[4i .. 4i+4) =
+ * {p, in-tile strike weight, weight of a bucket hit through the shared-memory
+ * cache, weight of a bucket hit read from global memory}, in units of 2^-16,
+ * 2^-8 or 2^-1 bit.  `out` is a HOST buffer of 4 * cap uint32_t; *n_out is the
+ * number of primes.  Blocking.  Errors: BNX_E_ARG, BNX_E_TRUNCATED, BNX_E_CUDA. */
+int bnx_log_weights(bnx_ctx *ctx, uint32_t tile_kind, uint32_t *out, size_t cap, size_t *n_out);
 
 /* ------------------------------------------------------------------------ */
 /* Searches                                                                    */
@@ -211,6 +267,15 @@ int bnx_search_chunked(bnx_ctx *ctx, uint64_t S, uint32_t chunk_log2, uint32_t k
  * that is not expected to run out). */
 int bnx_search_sorted(bnx_ctx *ctx, uint64_t S, uint32_t kinds, bnx_pair *out, size_t cap, size_t *n_out);
 
+/* Test hook for bnx_search_sorted's bounded wait: the next bnx_search_sorted
+ * call on this context has the first sort tile of its first pass keep its
+ * digit counts to itself, and every tile gives up waiting for them after
+ * spin_limit polls (1 .. 2^22), so the call returns BNX_E_TIMEOUT with no pair
+ * written (when the sort has at least two tiles, S > 7169).  The hook arms that one call only; the
+ * call after it runs normally.  Every index the sort writes stays in bounds
+ * and every wait ends; nothing here can stall the device.  Errors: BNX_E_ARG. */
+int bnx_arm_lookback_timeout(bnx_ctx *ctx, uint32_t spin_limit);
+
 /* Batched path: k intervals in one pipeline -- large-prime bucket fill, one
  * persistent sieve launch pulling segments from a device queue, verification
  * and a device sort -- replayed from a cached CUDA graph when the batch shape
@@ -226,19 +291,47 @@ int bnx_batch(bnx_ctx *ctx, const bnx_interval *iv, size_t k, bnx_pair *out, siz
 /* ------------------------------------------------------------------------ */
 
 typedef struct {
-    uint32_t max_active;      /* requests on the device at once (slots) */
+    uint32_t max_active;      /* requests on the device at once (slots, 1 .. 2^24) */
     uint32_t pad;
     uint64_t slice;           /* integers of each active request per iteration: at least
                                  slice, and an equal share of slice * max_active when
-                                 fewer than max_active requests are active */
-    uint64_t mem_budget;      /* bytes of workspace admission may commit (0: 90% of free HBM) */
+                                 fewer than max_active requests are active (any value
+                                 >= 1; a slice beyond a request's end takes the rest) */
+    uint64_t mem_budget;      /* bytes of device workspace the loop may hold (0: 90% of
+                                 the HBM free at start); the context's prime tables are
+                                 not counted */
 } bnx_server_cfg;
 
-/* Start the serving loop on a background host thread.  Each iteration takes
- * the next slice of every active request, runs them as one batched pipeline,
- * and admits waiting requests as slots and memory free up.
- * Errors: BNX_E_ARG, BNX_E_STATE (already running), BNX_E_NOMEM. */
+/* Counters of a serving loop (the current one, or the last after a stop). */
+typedef struct {
+    uint64_t submitted;      /* requests queued */
+    uint64_t completed;      /* requests finished, successfully or not */
+    uint64_t iterations;     /* batched pipeline runs */
+    uint64_t deferred;       /* requests that waited for memory while a slot was free */
+    uint64_t rejected;       /* requests whose first slice exceeds the budget even alone:
+                                they finish at once with BNX_E_NOMEM */
+    uint64_t budget_bytes;   /* the loop's workspace budget */
+    uint64_t ws_peak_bytes;  /* largest workspace held after an iteration (<= budget_bytes) */
+} bnx_server_stats;
+
+/* Start the serving loop on a background host thread.  Each iteration
+ *  - admits waiting requests in arrival order while a slot is free and an
+ *    iteration giving every admitted request `slice` integers fits the budget
+ *    (otherwise the request waits for memory);
+ *  - takes the next slice of every active request (shortened, down to one
+ *    queue segment, until the iteration's workspace fits the budget) and runs
+ *    all of them as one batched pipeline, the workspace sized under the budget.
+ * So the budget bounds the device memory the loop holds.
+ * Errors: BNX_E_ARG, BNX_E_STATE (already running), BNX_E_NOMEM, BNX_E_CUDA. */
 int bnx_server_start(bnx_ctx *ctx, const bnx_server_cfg *cfg);
+
+/* Counters of the serving loop (readable while it runs and after it stops). */
+int bnx_server_get_stats(bnx_ctx *ctx, bnx_server_stats *out);
+
+/* Device workspace, in bytes, that one batched run over these k intervals
+ * needs (bnx_batch sizes its workspace to at least this; the serving loop's
+ * admission uses the same figure).  `iv` is a HOST array.  Errors: BNX_E_ARG. */
+int bnx_workspace_bytes(bnx_ctx *ctx, const bnx_interval *iv, size_t k, uint64_t *bytes);
 
 /* Queue a request; *ticket identifies it.  Never blocks on the device. */
 int bnx_server_submit(bnx_ctx *ctx, const bnx_interval *iv, uint64_t *ticket);

@@ -50,6 +50,14 @@ class bnx_server_cfg(ctypes.Structure):
     _fields_ = [("max_active", u32), ("pad", u32), ("slice", u64), ("mem_budget", u64)]
 
 
+class bnx_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", u64), ("completed", u64), ("iterations", u64), ("deferred", u64),
+                ("rejected", u64), ("budget_bytes", u64), ("ws_peak_bytes", u64)]
+
+    def as_dict(self):
+        return {f: int(getattr(self, f)) for f, _ in self._fields_}
+
+
 class BnxError(RuntimeError):
     def __init__(self, code: int, msg: str):
         super().__init__(f"bnx error {code}: {msg}")
@@ -76,21 +84,28 @@ def lib(auto_build: bool = True):
         sig = {
             "bnx_create": ([P(vp), i32, u64, ctypes.c_char_p, vp], i32),
             "bnx_destroy": ([vp], None),
+            "bnx_tune_parse": ([ctypes.c_char_p, P(bnx_tune)], i32),
             "bnx_get_tune": ([vp, P(bnx_tune)], i32),
             "bnx_set_tune": ([vp, P(bnx_tune)], i32),
             "bnx_get_stats": ([vp, P(bnx_stats)], i32),
             "bnx_prime_count": ([vp, P(u64)], i32),
             "bnx_rad_segment": ([vp, u64, u64, vp, vp, vp], i32),
             "bnx_rad_segment_noalloc": ([u64, u64, vp, vp, vp], i32),
+            "bnx_log_weight": ([u64, u32], u32),
+            "bnx_log_weights": ([vp, u32, P(u32), sz, P(sz)], i32),
             "bnx_search": ([vp, u64, u64, u32, P(bnx_pair), sz, P(sz)], i32),
+            "bnx_search_segment": ([vp, u64, u32, u32, P(bnx_pair), sz, P(sz)], i32),
             "bnx_search_hash": ([vp, u64, u32, P(bnx_pair), sz, P(sz)], i32),
             "bnx_search_chunked": ([vp, u64, u32, u32, P(bnx_pair), sz, P(sz)], i32),
             "bnx_search_sorted": ([vp, u64, u32, P(bnx_pair), sz, P(sz)], i32),
             "bnx_batch": ([vp, P(bnx_interval), sz, P(bnx_pair), sz, P(sz), P(u64)], i32),
+            "bnx_arm_lookback_timeout": ([vp, u32], i32),
             "bnx_server_start": ([vp, P(bnx_server_cfg)], i32),
             "bnx_server_submit": ([vp, P(bnx_interval), P(u64)], i32),
             "bnx_server_poll": ([vp, u64, P(bnx_pair), sz, P(sz), P(ctypes.c_double)], i32),
             "bnx_server_stop": ([vp], i32),
+            "bnx_server_get_stats": ([vp, P(bnx_server_stats)], i32),
+            "bnx_workspace_bytes": ([vp, P(bnx_interval), sz, P(u64)], i32),
             "bnx_autotune": ([vp, P(bnx_interval), sz, i32, ctypes.c_char_p, sz], i32),
             "bnx_strerror": ([i32], ctypes.c_char_p),
             "bnx_last_error": ([], ctypes.c_char_p),
@@ -133,6 +148,13 @@ def bnx_destroy(ctx) -> None:
     lib().bnx_destroy(ctx)
 
 
+def bnx_tune_parse(json_text: str) -> bnx_tune:
+    """The tuning a JSON object gives (defaults for absent fields); raises on a bad object."""
+    t = bnx_tune()
+    _check(lib().bnx_tune_parse(json_text.encode(), ctypes.byref(t)))
+    return t
+
+
 def bnx_get_tune(ctx) -> bnx_tune:
     t = bnx_tune()
     _check(lib().bnx_get_tune(ctx, ctypes.byref(t)))
@@ -157,7 +179,7 @@ def bnx_prime_count(ctx) -> int:
 
 def bnx_rad_segment(ctx, lo: int, length: int, rad_out_ptr: int, sq_out_ptr: int | None = None,
                     stream: int | None = None) -> None:
-    """Device pointers in, asynchronous on `stream`."""
+    """Device pointers: asynchronous on `stream`; host pointers: returns once written."""
     _check(lib().bnx_rad_segment(ctx, lo, length, rad_out_ptr, sq_out_ptr or None, stream or None))
 
 
@@ -169,6 +191,26 @@ def bnx_rad_segment_noalloc(lo: int, length: int, rad_out_ptr: int, sq_out_ptr: 
     """Like bnx_rad_segment, for callers that cannot allocate device memory: no
     context, no allocation, fixed limits (length <= 2^18, lo + length <= 2^40)."""
     _check(lib().bnx_rad_segment_noalloc(lo, length, rad_out_ptr, sq_out_ptr or None, stream or None))
+
+
+def bnx_log_weight(p: int, frac_log2: int) -> int:
+    """Smallest L with 2^L > p^(2^frac_log2), in integers (host only)."""
+    return int(lib().bnx_log_weight(p, frac_log2))
+
+
+def bnx_log_weights(ctx, tile_kind: int = 3):
+    """Per prime of the context's table: (p, in-tile, cached-bucket, global-bucket) weights
+    of the log tile `tile_kind`, as the device computes them."""
+    n = sz()
+    rc = lib().bnx_log_weights(ctx, tile_kind, None, 0, ctypes.byref(n))
+    if rc not in (BNX_OK, BNX_E_TRUNCATED):
+        _check(rc)
+    cap = int(n.value)
+    buf = (u32 * (4 * max(cap, 1)))()
+    _check(lib().bnx_log_weights(ctx, tile_kind, buf, cap, ctypes.byref(n)))
+    import numpy as np
+
+    return np.frombuffer(buf, dtype=np.uint32)[:4 * cap].reshape(cap, 4).copy()
 
 
 def _grow_call(fn, cap=256):
@@ -189,6 +231,12 @@ def bnx_search(ctx, lo: int, hi: int, kinds: int = 3):
     return _pairs(buf, n)
 
 
+def bnx_search_segment(ctx, lo: int, length: int, kinds: int = 3):
+    """Pairs (m, n, kind) with lo <= n < lo + length (length < 2^32), sorted by (n, m, kind)."""
+    buf, n = _grow_call(lambda b, c, pn: lib().bnx_search_segment(ctx, lo, length, kinds, b, c, pn))
+    return _pairs(buf, n)
+
+
 def bnx_search_hash(ctx, S: int, kinds: int = 3):
     """Pairs (m, n, kind) with m < n < S by the device hash table."""
     buf, n = _grow_call(lambda b, c, pn: lib().bnx_search_hash(ctx, S, kinds, b, c, pn))
@@ -205,6 +253,11 @@ def bnx_search_sorted(ctx, S: int, kinds: int = 3):
     """Pairs (m, n, kind) with m < n < S by Algorithm 2 (device radix sort of the keys)."""
     buf, n = _grow_call(lambda b, c, pn: lib().bnx_search_sorted(ctx, S, kinds, b, c, pn))
     return _pairs(buf, n)
+
+
+def bnx_arm_lookback_timeout(ctx, spin_limit: int) -> None:
+    """Test hook: the next bnx_search_sorted call's look-back wait runs out (BNX_E_TIMEOUT)."""
+    _check(lib().bnx_arm_lookback_timeout(ctx, spin_limit))
 
 
 def make_intervals(intervals):
@@ -263,6 +316,20 @@ def bnx_server_stop(ctx) -> None:
     _check(lib().bnx_server_stop(ctx))
 
 
+def bnx_server_get_stats(ctx) -> dict:
+    st = bnx_server_stats()
+    _check(lib().bnx_server_get_stats(ctx, ctypes.byref(st)))
+    return st.as_dict()
+
+
+def bnx_workspace_bytes(ctx, intervals) -> int:
+    """Device workspace bytes one batched run over these intervals needs."""
+    arr = make_intervals(intervals)
+    v = u64()
+    _check(lib().bnx_workspace_bytes(ctx, arr, len(intervals), ctypes.byref(v)))
+    return int(v.value)
+
+
 def bnx_autotune(ctx, intervals, rounds: int = 2) -> str:
     arr = make_intervals(intervals)
     out = ctypes.create_string_buffer(512)
@@ -297,6 +364,9 @@ class Context:
     def search(self, lo, hi, kinds=3):
         return bnx_search(self.h, lo, hi, kinds)
 
+    def search_segment(self, lo, length, kinds=3):
+        return bnx_search_segment(self.h, lo, length, kinds)
+
     def search_hash(self, S, kinds=3):
         return bnx_search_hash(self.h, S, kinds)
 
@@ -326,6 +396,9 @@ class Context:
 
     def prime_count(self):
         return bnx_prime_count(self.h)
+
+    def log_weights(self, tile_kind=3):
+        return bnx_log_weights(self.h, tile_kind)
 
     def autotune(self, intervals, rounds=2):
         return bnx_autotune(self.h, intervals, rounds)

@@ -44,7 +44,13 @@ constexpr uint32_t kOsWarpItems = kOsTile / kOsWarps;      // consecutive record
 constexpr size_t kOsStageBytes = (size_t)kOsTile * 12;     // staged keys and values of one tile
 constexpr uint32_t kPasses = 4;
 constexpr uint32_t kLowBits = 32;  // the sort orders by bits 32..63 of h
-constexpr unsigned kErrLookback = 16u;  // a look-back wait ran out (never expected)
+// Error bit of a look-back wait that ran out in pass p: kErrLookback << p (never expected).
+// Each pass, and the pair-run kernel, return at once when an earlier pass set one: its
+// output is then incomplete, and a partial prefix can leave slots unwritten, which a
+// later pass would read.  Only finished kernels set the bits a kernel reads, so every
+// block of it sees the same value.
+constexpr unsigned kErrLookback = 16u;
+constexpr unsigned kErrLookbackAll = kErrLookback * 15u;  // the bits of all four passes
 constexpr uint32_t kSpinLimit = 1u << 22;
 
 // Look-back words: (state << 59) | value, state = 1 + 2 * pass + inclusive,
@@ -104,12 +110,16 @@ __global__ void k_a2_starts(const unsigned long long *hist, unsigned long long *
     }
 }
 
-// One stable pass over digit `pass` of h (bits 32 + 8 pass .. 32 + 8 pass + 7).
+// One stable pass over digit `pass` of h (bits 32 + 8 pass .. 32 + 8 pass + 7).  A
+// look-back wait gives up after spin_limit polls.  withhold (a test hook, 0 in normal
+// use) makes tile 0 keep its counts to itself, so that the waits on it run out: every
+// index still stays in bounds (a prefix can only fall short, and the keys of pass 0
+// are the real ones) and every wait ends.
 template <uint32_t pass>
 __global__ void __launch_bounds__(kOsThreads, 2)
     k_rs_onesweep(const unsigned long long *kin, const uint32_t *vin, unsigned long long *kout, uint32_t *vout,
                   uint64_t N, const unsigned long long *gstart, unsigned long long *look, unsigned int *tile_ctr,
-                  unsigned int *err) {
+                  unsigned int *err, uint32_t spin_limit, uint32_t withhold) {
     extern __shared__ unsigned long long stage[];  // kOsTile keys, then kOsTile values
     uint32_t *vstage = (uint32_t *)(stage + kOsTile);
     __shared__ uint32_t wcnt[kOsWarps][256];
@@ -118,9 +128,14 @@ __global__ void __launch_bounds__(kOsThreads, 2)
     __shared__ uint32_t s_tile;
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const uint32_t lt = (1u << lane) - 1;
-    if (tid == 0) s_tile = atomicAdd(tile_ctr, 1u);  // tiles are claimed in launch order
+    __shared__ bool s_abort;
+    if (tid == 0) {
+        s_tile = atomicAdd(tile_ctr, 1u);  // tiles are claimed in launch order
+        s_abort = pass > 0 && (*(volatile unsigned int *)err & (kErrLookback * ((1u << pass) - 1u))) != 0u;
+    }
     for (uint32_t d = lane; d < 256; d += 32) wcnt[warp][d] = 0;
     __syncthreads();
+    if (s_abort) return;
     const uint64_t t = s_tile;
     const uint64_t t0 = t * kOsTile;
     const uint64_t w0 = t0 + (uint64_t)warp * kOsWarpItems;
@@ -141,7 +156,7 @@ __global__ void __launch_bounds__(kOsThreads, 2)
         uint32_t tot = 0;
         for (uint32_t w = 0; w < kOsWarps; w++) tot += wcnt[w][tid];
         unsigned long long *mine = look + t * 256 + tid;
-        st_volatile(mine, lb_word(pass, t == 0, tot));
+        if (!(pass == 0 && withhold && t == 0)) st_volatile(mine, lb_word(pass, t == 0, tot));
         // block-local start of the digit, then each warp's first slot
         uint32_t inc = tot;
         for (int o = 1; o < 32; o <<= 1) {
@@ -165,12 +180,12 @@ __global__ void __launch_bounds__(kOsThreads, 2)
             unsigned long long w = ld_volatile(p);
             uint32_t spins = 0;
             while ((w >> 59) == 0 || (((w >> 59) - 1) >> 1) != pass) {
-                if (++spins > kSpinLimit) break;
+                if (++spins > spin_limit) break;
                 __nanosleep(64);
                 w = ld_volatile(p);
             }
-            if (spins > kSpinLimit) {  // a tile before this one never published: give up, flag it
-                atomicOr(err, kErrLookback);
+            if (spins > spin_limit) {  // a tile before this one never published: give up, flag it
+                atomicOr(err, kErrLookback << pass);
                 break;
             }
             excl += w & ((1ull << 59) - 1);
@@ -223,6 +238,7 @@ __global__ void __launch_bounds__(kOsThreads, 2)
 constexpr uint32_t kGroupRounds = 32;
 __global__ void k_a2_groups(const unsigned long long *key, const uint32_t *val, uint64_t N, const uint64_t *rad,
                             uint32_t kinds, PairDev *pairs, uint64_t cap, unsigned long long *np, unsigned int *err) {
+    if (*(volatile unsigned int *)err & kErrLookbackAll) return;  // the sort is incomplete
     const uint32_t lane = threadIdx.x & 31;
     const uint64_t nwarps = ((uint64_t)gridDim.x * blockDim.x) >> 5;
     const uint64_t chunk = 32ull * kGroupRounds;
@@ -282,6 +298,14 @@ __global__ void k_a2_sort(const PairDev *in, const unsigned long long *np_dev, u
 
 using namespace bnx;
 
+extern "C" int bnx_arm_lookback_timeout(bnx_ctx *c, uint32_t spin_limit) {
+    if (!c) return fail(BNX_E_ARG, "NULL context");
+    if (spin_limit < 1 || spin_limit > kSpinLimit) return fail(BNX_E_ARG, "spin_limit must be in [1, 2^22]");
+    std::lock_guard<std::mutex> g(c->mu);
+    c->lb_spin_limit = spin_limit;
+    return BNX_OK;
+}
+
 extern "C" int bnx_search_sorted(bnx_ctx *c, uint64_t S, uint32_t kinds, bnx_pair *out, size_t cap, size_t *n_out) {
     if (!c) return fail(BNX_E_ARG, "NULL context");
     if (S < 3 || S > (1ull << 32) || S >= c->max_hi) return fail(BNX_E_ARG, "need 3 <= S <= 2^32 and S < max_hi");
@@ -316,6 +340,10 @@ extern "C" int bnx_search_sorted(bnx_ctx *c, uint64_t S, uint32_t kinds, bnx_pai
     CUDA_TRY(cudaFuncSetAttribute(k_rs_onesweep<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOsStageBytes));
     CUDA_TRY(cudaFuncSetAttribute(k_rs_onesweep<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kOsStageBytes));
     static_assert(kPasses == 4, "one instantiation per pass");
+    // the look-back test hook arms one call only
+    const uint32_t spin_limit = c->lb_spin_limit ? c->lb_spin_limit : kSpinLimit;
+    const uint32_t withhold = c->lb_spin_limit ? 1u : 0u;
+    c->lb_spin_limit = 0;
     CUDA_TRY(cudaEventRecord(c->ev0, st));
     CUDA_TRY(cudaMemsetAsync(misc.p, 0, 8 * kMiscWords, st));
     CUDA_TRY(cudaMemsetAsync(look.p, 0, 8 * 256 * nt, st));
@@ -338,10 +366,10 @@ extern "C" int bnx_search_sorted(bnx_ctx *c, uint64_t S, uint32_t kinds, bnx_pai
         unsigned int *tc = tile_ctr + pass;
         const unsigned grid_t = (unsigned)nt;
         switch (pass) {
-            case 0: k_rs_onesweep<0><<<grid_t, kOsThreads, kOsStageBytes, st>>>(ki, vi, ko, vo, N, gs, lk, tc, err_dev); break;
-            case 1: k_rs_onesweep<1><<<grid_t, kOsThreads, kOsStageBytes, st>>>(ki, vi, ko, vo, N, gs, lk, tc, err_dev); break;
-            case 2: k_rs_onesweep<2><<<grid_t, kOsThreads, kOsStageBytes, st>>>(ki, vi, ko, vo, N, gs, lk, tc, err_dev); break;
-            default: k_rs_onesweep<3><<<grid_t, kOsThreads, kOsStageBytes, st>>>(ki, vi, ko, vo, N, gs, lk, tc, err_dev); break;
+            case 0: k_rs_onesweep<0><<<grid_t, kOsThreads, kOsStageBytes, st>>>(ki, vi, ko, vo, N, gs, lk, tc, err_dev, spin_limit, withhold); break;
+            case 1: k_rs_onesweep<1><<<grid_t, kOsThreads, kOsStageBytes, st>>>(ki, vi, ko, vo, N, gs, lk, tc, err_dev, spin_limit, 0u); break;
+            case 2: k_rs_onesweep<2><<<grid_t, kOsThreads, kOsStageBytes, st>>>(ki, vi, ko, vo, N, gs, lk, tc, err_dev, spin_limit, 0u); break;
+            default: k_rs_onesweep<3><<<grid_t, kOsThreads, kOsStageBytes, st>>>(ki, vi, ko, vo, N, gs, lk, tc, err_dev, spin_limit, 0u); break;
         }
         std::swap(kin, kout);
         std::swap(vin, vout);
@@ -358,7 +386,7 @@ extern "C" int bnx_search_sorted(bnx_ctx *c, uint64_t S, uint32_t kinds, bnx_pai
         CUDA_TRY(cudaMemcpyAsync(h, misc.p, 16, cudaMemcpyDeviceToHost, st));
         CUDA_TRY(cudaEventRecord(c->ev1, st));
         CUDA_TRY(cudaStreamSynchronize(st));
-        if ((unsigned int)h[1] & kErrLookback) return fail(BNX_E_TIMEOUT, "radix sort look-back wait ran out");
+        if ((unsigned int)h[1] & kErrLookbackAll) return fail(BNX_E_TIMEOUT, "radix sort look-back wait ran out");
         if (h[0] > pcap) {
             pcap = h[0] + 64;
             continue;

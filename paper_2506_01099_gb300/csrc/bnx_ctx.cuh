@@ -62,6 +62,7 @@ struct bnx_ctx {
     // workspace
     bnx::DevBuf ivs, n_iv, ctr, bcnt, seg_iv, boff, bent, scan_tmp, cand, surv, pairs, pairs_sorted, offsets;
     bnx::DevBuf hkeys, hheads, hnext, hslot;
+    bnx::DevBuf rad_stage;  // device staging of bnx_rad_segment's results for host buffers
     size_t surv_want = 1 << 16, pair_want = 1 << 12, cand_want = 1 << 16;
     bnx::Counters *h_ctr = nullptr;  // pinned
     bnx::IvDev *h_ivs = nullptr;     // pinned staging
@@ -80,11 +81,14 @@ struct bnx_ctx {
     bool capturing = false;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_s0 = nullptr, ev_s1 = nullptr;
 
+    uint32_t lb_spin_limit = 0;  // nonzero: the next bnx_search_sorted runs the look-back test hook
     bnx::SieveCfg sieve_cfg[12];  // per (mode, tile: exact, log u32, log u16, log u8)
     bnx_stats stats{};
     std::mutex mu;
     bnx::Server *server = nullptr;
     std::atomic<bool> serving{false};
+    std::mutex stats_mu;           // guards srv_stats (written by the serving thread)
+    bnx_server_stats srv_stats{};  // of the current or last serving loop
 
     uint32_t n_sched() const { return bnx::sched_length(tune.tile_log2, h_spp_q.data(), n_spp); }
     uint32_t seg_log2() const {
@@ -96,7 +100,8 @@ struct bnx_ctx {
     bool server_running() const { return serving.load(); }
     std::vector<bnx::DevBuf *> all_bufs() {
         return {&primes, &spp,   &lpp,          &tmp_counts, &ivs,  &n_iv,  &ctr,  &bcnt,  &seg_iv, &boff,  &bent,
-                &scan_tmp, &cand, &surv, &pairs, &pairs_sorted, &offsets, &hkeys, &hheads, &hnext, &hslot};
+                &scan_tmp, &cand, &surv, &pairs, &pairs_sorted, &offsets, &hkeys, &hheads, &hnext, &hslot,
+                &rad_stage};
     }
 };
 
@@ -104,7 +109,10 @@ namespace bnx {
 int build_pp_tables(bnx_ctx *c);
 uint64_t bucket_bound(const bnx_ctx *c, uint64_t lo, uint64_t hi, uint64_t nseg);
 int plan_host(bnx_ctx *c, const IvDev *iv, size_t k, PlanTotals *t);
-int ensure_ws(bnx_ctx *c, const PlanTotals &t, size_t k);
+int ensure_ws(bnx_ctx *c, const PlanTotals &t, size_t k, uint64_t budget = 0);
+int ensure_staging(bnx_ctx *c, size_t k);                          // pinned host staging of k intervals
+uint64_t ws_need_bytes(bnx_ctx *c, const PlanTotals &t, size_t k);  // bytes a run needs
+uint64_t ws_footprint(bnx_ctx *c);                                   // bytes the workspace holds
 Plan make_plan(const bnx_ctx *c);
 int sieve_config(bnx_ctx *c, int mode, int *grid, int *threads, size_t *smem);
 int record_pipeline(bnx_ctx *c, int mode, cudaStream_t s, bool timing);
@@ -112,7 +120,8 @@ int run_search(bnx_ctx *c, size_t k, bool use_graph);
 int check_counters(bnx_ctx *c, bool *rerun);
 void fill_stats(bnx_ctx *c, uint64_t integers);
 int validate_interval(const bnx_ctx *c, uint64_t lo, uint64_t hi, uint32_t kinds);
-int search_staged(bnx_ctx *c, size_t k, bnx_pair *out, size_t cap, size_t *n_out, uint64_t *offsets);
+int search_staged(bnx_ctx *c, size_t k, bnx_pair *out, size_t cap, size_t *n_out, uint64_t *offsets,
+                  uint64_t budget = 0);
 int rad_segment_unlocked(bnx_ctx *c, uint64_t lo, uint64_t len, uint64_t *rad_out, uint64_t *sq_out,
                          cudaStream_t s);
 }  // namespace bnx

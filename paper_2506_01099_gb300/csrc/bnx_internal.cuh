@@ -23,14 +23,82 @@ namespace bnx {
 constexpr int kMaxSpp = 256;    // in-tile prime powers per context
 constexpr int kMaxThreads = 1024;
 
-// Fixed-point scale of the log-domain tile: lg(p) = floor(log2(p) * 2^16) + 1,
-// strictly above log2(p) * 2^16.
+// Fixed-point scale of the u32 log-domain tile: weights in units of 2^-16 bit.
 constexpr uint32_t kLogFrac = 16;
+
+// ---- log weights of the log-domain tiles, in integers only ----------------
+// The log tiles add, per prime-power strike at x, a weight w(p) that must be at
+// least F log2 p (F = 2^f units per bit): then their sum is an upper bound of
+// F log2 of the odd square part, and rejecting n on that bound loses nothing.
+// log_weight(p, f) is the smallest integer L with 2^L > p^(2^f), i.e. the bit
+// length of p^(2^f) = floor(2^f log2 p) + 1 (p odd, so 2^f log2 p is never an
+// integer), computed without floating point: write p = 2^e m with m in [1, 2)
+// as a 62-bit fraction M / 2^62 and square it f times, rounding each square UP
+// to 62 fractional bits and halving (again rounding up) when it reaches 2; k
+// collects the halvings as binary digits.  By induction 2^k (M / 2^62) >=
+// m^(2^i) after i squarings, so m^(2^f) < 2^(k+1) and L = e 2^f + k + 1 >
+// 2^f log2 p: the weight can only over-estimate.  It equals the exact bit
+// length unless some 2^i log2 m lies within the accumulated rounding (about
+// 2^(i-61)) of an integer; the tests compare it with exact big-integer bit
+// lengths for every prime the tables hold.  M < 2^63 throughout, so M^2 <
+// 2^126 and the rounded square fits 64 bits.
+__host__ __device__ inline uint32_t log_weight(uint64_t p, uint32_t f) {
+    if (p < 2 || p >= (1ull << 32) || f > 16) return 0;
+#ifdef __CUDA_ARCH__
+    const uint32_t e = 63u - (uint32_t)__clzll((long long)p);
+#else
+    const uint32_t e = 63u - (uint32_t)__builtin_clzll(p);
+#endif
+    uint64_t M = p << (62 - e);
+    uint32_t k = 0;
+    for (uint32_t i = 0; i < f; i++) {
+#ifdef __CUDA_ARCH__
+        const uint64_t hi = __umul64hi(M, M), lo = M * M;
+#else
+        const unsigned __int128 sq = (unsigned __int128)M * M;
+        const uint64_t hi = (uint64_t)(sq >> 64), lo = (uint64_t)sq;
+#endif
+        // ceil(M^2 / 2^62): the square in 62 fractional bits, rounded up
+        uint64_t S = (hi << 2) | (lo >> 62);
+        if (lo & ((1ull << 62) - 1)) S++;
+        k <<= 1;
+        if (S >> 63) {  // the square reached 2: halve it, rounding up
+            S = (S >> 1) + (S & 1);
+            k |= 1;
+        }
+        M = S;
+    }
+    return (e << f) + k + 1;
+}
+
+// Weight of an in-tile strike (q = p^k <= Q) in the tile's units: VB bytes per
+// tile value; units of 2^-1 bit (VB = 1), 2^-8 (VB = 2) or 2^-16 (VB = 4).
+template <int VB>
+__host__ __device__ inline uint32_t tile_weight(uint64_t p) {
+    return log_weight(p, VB == 1 ? 1u : VB == 2 ? 8u : 16u);
+}
+// The 12-bit weight field of a bucket entry cached in shared memory: the u8
+// tile's own weight (at most 2 * 21 + 1 for p < 2^21), else the weight in
+// units of 2^-7 bit (below 2^12 for p < 2^21), scaled up by cache_to_tile.
+template <int VB>
+__host__ __device__ inline uint32_t cache_weight(uint64_t p) {
+    return VB == 1 ? log_weight(p, 1) : log_weight(p, 7);
+}
+template <int VB>
+__host__ __device__ inline uint32_t cache_to_tile(uint32_t w) {
+    return VB == 1 ? w : VB == 2 ? w << 1 : w << 9;
+}
+// Weight of a bucket hit (a large prime power) in the tile's units, whether it
+// comes from the shared cache or from global memory.
+template <int VB>
+__host__ __device__ inline uint32_t bucket_weight(uint64_t p) {
+    return cache_to_tile<VB>(cache_weight<VB>(p));
+}
 
 struct SmallPP {
     uint32_t q;   // p^k
     uint32_t p;
-    uint32_t lg;  // log2(p) rounded up in units of 2^-16
+    uint32_t lg;  // log_weight(p, 16): the u32 tile's weight, units of 2^-16
     uint32_t k;   // exponent
 };
 
@@ -168,6 +236,8 @@ int sieve_log_occupancy(int mode, int threads, int vb, size_t smem, int *ctas_pe
 // exact check of the log tile's candidates: survivors into P.surv
 void launch_cand(const Plan &P, int mode, int grid, cudaStream_t s);
 size_t sieve_log_smem_bytes(uint32_t tile_log2, uint32_t nspp, uint32_t nsched, int vb);
+// the weights each prime of the table gets in the log tile of vb bytes per value (4 u32 each)
+void launch_log_weights(const uint32_t *primes, uint32_t np, int vb, uint32_t *out, cudaStream_t s);
 size_t sieve_smem_bytes(uint32_t tile_log2, uint32_t nspp, uint32_t nsched);
 uint32_t sched_length(uint32_t tile_log2, const uint32_t *q, uint32_t nspp);
 

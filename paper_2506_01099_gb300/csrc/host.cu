@@ -75,7 +75,11 @@ static int tune_check(const bnx_tune *t) {
     return BNX_OK;
 }
 
-// Minimal reader for a flat JSON object of non-negative integers.
+// Reader for a flat JSON object whose values are non-negative integers: the
+// bnx_tune field names, plus "ms" (a number, ignored), which bnx_autotune writes
+// beside them.  Unknown or repeated keys, values that are not integers or do not
+// fit 32 bits, and anything after the closing brace are errors; fields that are
+// absent keep their value in *t.
 static int parse_tune_json(const char *s, bnx_tune *t) {
     struct F {
         const char *name;
@@ -85,20 +89,72 @@ static int parse_tune_json(const char *s, bnx_tune *t) {
                   {"threads", &t->threads},
                   {"ctas_per_sm", &t->ctas_per_sm},
                   {"small_q_log2", &t->small_q_log2},
-                  {"tile_kind", &t->tile_kind}};
-    for (const F &f : fields) {
-        std::string key = std::string("\"") + f.name + "\"";
-        const char *p = strstr(s, key.c_str());
-        if (!p) continue;
-        p += key.size();
+                  {"tile_kind", &t->tile_kind},
+                  {"ms", nullptr}};
+    constexpr int nf = sizeof fields / sizeof fields[0];
+    bool seen[nf] = {};
+    auto ws = [](const char *&p) {
         while (*p == ' ' || *p == '\t' || *p == '\n' || *p == '\r') p++;
-        if (*p != ':') return fail(BNX_E_ARG, "tune JSON: expected ':' after %s", f.name);
+    };
+    const char *p = s;
+    ws(p);
+    if (*p++ != '{') return fail(BNX_E_ARG, "tune JSON: expected '{'");
+    ws(p);
+    if (*p == '}') {
         p++;
-        while (*p == ' ' || *p == '\t' || *p == '\n' || *p == '\r') p++;
-        if (*p < '0' || *p > '9') return fail(BNX_E_ARG, "tune JSON: %s is not a non-negative integer", f.name);
-        unsigned long v = strtoul(p, nullptr, 10);
-        *f.dst = (uint32_t)v;
+    } else {
+        for (;;) {
+            ws(p);
+            if (*p++ != '"') return fail(BNX_E_ARG, "tune JSON: expected a quoted key");
+            const char *k0 = p;
+            while (*p && *p != '"') p++;
+            if (*p != '"') return fail(BNX_E_ARG, "tune JSON: unterminated key");
+            const std::string key(k0, (size_t)(p - k0));
+            p++;
+            int f = -1;
+            for (int i = 0; i < nf; i++)
+                if (key == fields[i].name) f = i;
+            if (f < 0) return fail(BNX_E_ARG, "tune JSON: unknown field \"%s\"", key.c_str());
+            if (seen[f]) return fail(BNX_E_ARG, "tune JSON: field \"%s\" given twice", key.c_str());
+            seen[f] = true;
+            ws(p);
+            if (*p++ != ':') return fail(BNX_E_ARG, "tune JSON: expected ':' after \"%s\"", key.c_str());
+            ws(p);
+            if (*p < '0' || *p > '9') return fail(BNX_E_ARG, "tune JSON: %s is not a non-negative number", key.c_str());
+            uint64_t v = 0;
+            while (*p >= '0' && *p <= '9') {
+                v = v * 10 + (uint64_t)(*p++ - '0');
+                if (v > 0xffffffffull) return fail(BNX_E_ARG, "tune JSON: %s does not fit 32 bits", key.c_str());
+            }
+            if (fields[f].dst) {
+                if (*p == '.' || *p == 'e' || *p == 'E')
+                    return fail(BNX_E_ARG, "tune JSON: %s is not an integer", key.c_str());
+                *fields[f].dst = (uint32_t)v;
+            } else {  // "ms": the fraction and exponent of a JSON number
+                if (*p == '.') {
+                    p++;
+                    while (*p >= '0' && *p <= '9') p++;
+                }
+                if (*p == 'e' || *p == 'E') {
+                    p++;
+                    if (*p == '+' || *p == '-') p++;
+                    while (*p >= '0' && *p <= '9') p++;
+                }
+            }
+            ws(p);
+            if (*p == ',') {
+                p++;
+                continue;
+            }
+            if (*p == '}') {
+                p++;
+                break;
+            }
+            return fail(BNX_E_ARG, "tune JSON: expected ',' or '}' after \"%s\"", key.c_str());
+        }
     }
+    ws(p);
+    if (*p) return fail(BNX_E_ARG, "tune JSON: text after the closing brace");
     return tune_check(t);
 }
 
@@ -203,36 +259,94 @@ int plan_host(bnx_ctx *c, const IvDev *iv, size_t k, PlanTotals *t) {
     return BNX_OK;
 }
 
-int ensure_ws(bnx_ctx *c, const PlanTotals &t, size_t k) {
-    int rc;
-    bool changed = false;
-    auto need = [&](DevBuf &b, size_t bytes) -> int {
-        if (b.bytes >= bytes) return BNX_OK;
-        changed = true;
-        return grow(b, bytes + bytes / 4);
+// The workspace buffers of one pipeline run and the bytes each needs for a run
+// with plan totals t over k intervals.
+static int ws_needs(bnx_ctx *c, const PlanTotals &t, size_t k, DevBuf **buf, size_t *bytes) {
+    int n = 0;
+    auto add = [&](DevBuf &b, size_t v) {
+        buf[n] = &b;
+        bytes[n++] = v;
     };
-    if ((rc = need(c->ivs, sizeof(IvDev) * (k + 1)))) return rc;
-    if ((rc = need(c->offsets, sizeof(uint64_t) * (k + 2)))) return rc;
-    if ((rc = need(c->bcnt, sizeof(uint32_t) * (t.segs + 1)))) return rc;
-    if ((rc = need(c->seg_iv, sizeof(uint32_t) * (t.segs + 1)))) return rc;
-    if ((rc = need(c->boff, sizeof(unsigned long long) * (t.segs + 2)))) return rc;
-    if ((rc = need(c->scan_tmp, sizeof(unsigned long long) * (t.segs / 4096 + 2)))) return rc;
-    if ((rc = need(c->bent, sizeof(uint2) * (t.buckets + 1)))) return rc;
-    if ((rc = need(c->cand, sizeof(Cand) * c->cand_want))) return rc;
-    if ((rc = need(c->surv, sizeof(Survivor) * c->surv_want))) return rc;
-    if ((rc = need(c->pairs, sizeof(PairDev) * c->pair_want))) return rc;
-    if ((rc = need(c->pairs_sorted, sizeof(PairDev) * c->pair_want))) return rc;
-    if (changed) c->graph_valid = false;
-    if (k + 1 > c->h_ivs_cap) {
-        if (c->h_ivs) cudaFreeHost(c->h_ivs);
-        c->h_ivs = nullptr;
-        c->h_ivs_cap = 0;
-        if (cudaMallocHost(&c->h_ivs, sizeof(IvDev) * (k + 1) * 2) != cudaSuccess) {
-            cudaGetLastError();
-            return fail(BNX_E_NOMEM, "pinned host allocation failed");
-        }
-        c->h_ivs_cap = (k + 1) * 2;
+    add(c->ivs, sizeof(IvDev) * (k + 1));
+    add(c->offsets, sizeof(uint64_t) * (k + 2));
+    add(c->bcnt, sizeof(uint32_t) * (t.segs + 1));
+    add(c->seg_iv, sizeof(uint32_t) * (t.segs + 1));
+    add(c->boff, sizeof(unsigned long long) * (t.segs + 2));
+    add(c->scan_tmp, sizeof(unsigned long long) * (t.segs / 4096 + 2));
+    add(c->bent, sizeof(uint2) * (t.buckets + 1));
+    add(c->cand, sizeof(Cand) * c->cand_want);
+    add(c->surv, sizeof(Survivor) * c->surv_want);
+    add(c->pairs, sizeof(PairDev) * c->pair_want);
+    add(c->pairs_sorted, sizeof(PairDev) * c->pair_want);
+    return n;
+}
+constexpr int kWsBufs = 11;
+
+uint64_t ws_need_bytes(bnx_ctx *c, const PlanTotals &t, size_t k) {
+    DevBuf *b[kWsBufs];
+    size_t v[kWsBufs];
+    const int n = ws_needs(c, t, k, b, v);
+    uint64_t sum = 0;
+    for (int i = 0; i < n; i++) sum += v[i];
+    return sum;
+}
+
+uint64_t ws_footprint(bnx_ctx *c) {
+    const PlanTotals t0{0, 0, 0, 0};
+    DevBuf *b[kWsBufs];
+    size_t v[kWsBufs];
+    const int n = ws_needs(c, t0, 0, b, v);
+    uint64_t sum = 0;
+    for (int i = 0; i < n; i++) sum += b[i]->bytes;
+    return sum;
+}
+
+// Grow the workspace to fit a run.  A grown buffer gets a quarter more than it
+// needs, so that batches that grow slowly do not reallocate every time.  With a
+// budget (bytes, 0 = none) the workspace never exceeds it: when the usual growth
+// would, every buffer is sized to exactly what the run needs (larger leftovers
+// of earlier runs are freed first), and a run that needs more than the budget
+// fails with BNX_E_NOMEM before anything is allocated.
+int ensure_ws(bnx_ctx *c, const PlanTotals &t, size_t k, uint64_t budget) {
+    DevBuf *b[kWsBufs];
+    size_t v[kWsBufs];
+    const int n = ws_needs(c, t, k, b, v);
+    uint64_t grown = 0, exact = 0;
+    for (int i = 0; i < n; i++) {
+        grown += b[i]->bytes >= v[i] ? b[i]->bytes : v[i] + v[i] / 4;
+        exact += v[i];
     }
+    const bool tight = budget && grown > budget;
+    if (tight && exact > budget)
+        return fail(BNX_E_NOMEM, "the run needs %llu bytes of workspace, the budget is %llu",
+                    (unsigned long long)exact, (unsigned long long)budget);
+    bool changed = false;
+    int rc;
+    for (int i = 0; i < n; i++)
+        if (tight && b[i]->bytes > v[i]) {
+            release(*b[i]);
+            changed = true;
+        }
+    for (int i = 0; i < n; i++) {
+        if (b[i]->bytes >= v[i]) continue;
+        changed = true;
+        if ((rc = grow(*b[i], tight ? v[i] : v[i] + v[i] / 4))) return rc;
+    }
+    if (changed) c->graph_valid = false;
+    return ensure_staging(c, k);
+}
+
+// Pinned host staging for the intervals of a run of k intervals.
+int ensure_staging(bnx_ctx *c, size_t k) {
+    if (k + 1 <= c->h_ivs_cap) return BNX_OK;
+    if (c->h_ivs) cudaFreeHost(c->h_ivs);
+    c->h_ivs = nullptr;
+    c->h_ivs_cap = 0;
+    if (cudaMallocHost(&c->h_ivs, sizeof(IvDev) * (k + 1) * 2) != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BNX_E_NOMEM, "pinned host allocation failed");
+    }
+    c->h_ivs_cap = (k + 1) * 2;
     return BNX_OK;
 }
 
@@ -459,11 +573,12 @@ int validate_interval(const bnx_ctx *c, uint64_t lo, uint64_t hi, uint32_t kinds
 
 // Search the intervals staged in c->h_ivs[0..k), retrying on capacity
 // overflow; copies the sorted pairs (and per-interval offsets) to the host.
-int search_staged(bnx_ctx *c, size_t k, bnx_pair *out, size_t cap, size_t *n_out, uint64_t *offsets) {
+int search_staged(bnx_ctx *c, size_t k, bnx_pair *out, size_t cap, size_t *n_out, uint64_t *offsets,
+                  uint64_t budget) {
     PlanTotals t;
     plan_host(c, c->h_ivs, k, &t);
     for (int attempt = 0; attempt < 4; attempt++) {
-        int rc = ensure_ws(c, t, k);
+        int rc = ensure_ws(c, t, k, budget);
         if (rc) return rc;
         rc = run_search(c, k, true);
         if (rc) return rc;
@@ -510,6 +625,15 @@ const char *bnx_strerror(int code) {
 }
 
 const char *bnx_last_error(void) { return g_last_error.c_str(); }
+
+int bnx_tune_parse(const char *json, bnx_tune *out) {
+    if (!json || !out) return fail(BNX_E_ARG, "NULL argument");
+    bnx_tune t;
+    tune_defaults(&t);
+    const int rc = parse_tune_json(json, &t);
+    if (rc == BNX_OK) *out = t;
+    return rc;
+}
 
 int bnx_create(bnx_ctx **out, int device, uint64_t max_hi, const char *tune_json, void *stream) {
     if (!out) return fail(BNX_E_ARG, "out is NULL");
@@ -614,14 +738,53 @@ int bnx_prime_count(const bnx_ctx *c, uint64_t *out) {
     return BNX_OK;
 }
 
+// Whether a caller's buffer is host memory that the kernels cannot write (pageable,
+// or pinned: both are staged through device memory and copied).
+static int host_buffer(const void *p, bool *host) {
+    cudaPointerAttributes a;
+    cudaError_t e = cudaPointerGetAttributes(&a, p);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BNX_E_CUDA, "cudaPointerGetAttributes: %s", cudaGetErrorString(e));
+    }
+    *host = a.type == cudaMemoryTypeHost || a.type == cudaMemoryTypeUnregistered;
+    return BNX_OK;
+}
+
 int bnx_rad_segment(bnx_ctx *c, uint64_t lo, uint64_t len, uint64_t *rad_out, uint64_t *sq_out, void *stream) {
     if (!c || !rad_out) return fail(BNX_E_ARG, "NULL argument");
-    if (lo < 1 || len < 1 || len > (1ull << 31) || lo + len > c->max_hi)
+    // (lo > max_hi - len, not lo + len > max_hi: the sum could wrap)
+    if (lo < 1 || len < 1 || len > (1ull << 31) || len > c->max_hi || lo > c->max_hi - len)
         return fail(BNX_E_ARG, "need 1 <= lo, 1 <= len <= 2^31, lo + len <= max_hi");
     if (c->server_running()) return fail(BNX_E_STATE, "the serving loop owns the context");
     std::lock_guard<std::mutex> g(c->mu);
     cudaSetDevice(c->device);
-    return rad_segment_unlocked(c, lo, len, rad_out, sq_out, stream ? (cudaStream_t)stream : c->stream);
+    cudaStream_t s = stream ? (cudaStream_t)stream : c->stream;
+    bool host = false, host_sq = false;
+    int rc = host_buffer(rad_out, &host);
+    if (rc == BNX_OK && sq_out) rc = host_buffer(sq_out, &host_sq);
+    if (rc) return rc;
+    if (sq_out && host != host_sq) return fail(BNX_E_ARG, "rad_out and sq_out must both be host or both device buffers");
+    if (!host) return rad_segment_unlocked(c, lo, len, rad_out, sq_out, s);
+    // host buffers: sieve into device staging, copy back, and wait
+    const size_t bytes = sizeof(uint64_t) * len;
+    if ((rc = grow(c->rad_stage, sq_out ? 2 * bytes : bytes))) return rc;
+    uint64_t *d_rad = (uint64_t *)c->rad_stage.p, *d_sq = sq_out ? d_rad + len : nullptr;
+    rc = rad_segment_unlocked(c, lo, len, d_rad, d_sq, s);
+    if (rc == BNX_OK) {
+        cudaError_t e = cudaMemcpyAsync(rad_out, d_rad, bytes, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess && sq_out) e = cudaMemcpyAsync(sq_out, d_sq, bytes, cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            cudaGetLastError();
+            rc = fail(BNX_E_CUDA, "copy of the radicals to the host: %s", cudaGetErrorString(e));
+        }
+    }
+    if (c->rad_stage.bytes > ((size_t)1 << 28)) {  // a large staging buffer is not kept
+        cudaStreamSynchronize(s);
+        release(c->rad_stage);
+    }
+    return rc;
 }
 
 }  // extern "C"
@@ -656,8 +819,40 @@ int rad_segment_unlocked(bnx_ctx *c, uint64_t lo, uint64_t len, uint64_t *rad_ou
 
 extern "C" {
 
-int bnx_search(bnx_ctx *c, uint64_t lo, uint64_t hi, uint32_t kinds, bnx_pair *out, size_t cap, size_t *n_out) {
-    if (!c) return fail(BNX_E_ARG, "NULL context");
+uint32_t bnx_log_weight(uint64_t p, uint32_t frac_log2) { return log_weight(p, frac_log2); }
+
+int bnx_log_weights(bnx_ctx *c, uint32_t tile_kind, uint32_t *out, size_t cap, size_t *n_out) {
+    if (!c || !n_out) return fail(BNX_E_ARG, "NULL argument");
+    if (tile_kind != kTileLog32 && tile_kind != kTileLog16 && tile_kind != kTileLog8)
+        return fail(BNX_E_ARG, "tile_kind must be 0, 2 or 3 (a log-domain tile)");
+    if (c->server_running()) return fail(BNX_E_STATE, "the serving loop owns the context");
+    std::lock_guard<std::mutex> g(c->mu);
+    cudaSetDevice(c->device);
+    *n_out = c->np;
+    const size_t ncopy = std::min<size_t>(c->np, cap);
+    if (ncopy == 0) return c->np > cap ? fail(BNX_E_TRUNCATED, "%u primes, buffer holds %zu", c->np, cap) : BNX_OK;
+    if (!out) return fail(BNX_E_ARG, "out is NULL");
+    DevBuf w;
+    int rc = grow(w, sizeof(uint32_t) * 4 * (size_t)c->np);
+    if (rc) return rc;
+    const int vb = tile_kind == kTileLog8 ? 1 : tile_kind == kTileLog16 ? 2 : 4;
+    launch_log_weights((const uint32_t *)c->primes.p, c->np, vb, (uint32_t *)w.p, c->stream);
+    cudaError_t e = cudaGetLastError();
+    if (e == cudaSuccess) e = cudaMemcpyAsync(out, w.p, sizeof(uint32_t) * 4 * ncopy, cudaMemcpyDeviceToHost, c->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+    release(w);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BNX_E_CUDA, "log weights: %s", cudaGetErrorString(e));
+    }
+    return c->np > cap ? fail(BNX_E_TRUNCATED, "%u primes, buffer holds %zu", c->np, cap) : BNX_OK;
+}
+
+}  // extern "C"
+
+// One n-range through the staged pipeline (bnx_search and bnx_search_segment).
+static int search_one(bnx_ctx *c, uint64_t lo, uint64_t hi, uint32_t kinds, bnx_pair *out, size_t cap,
+                      size_t *n_out) {
     int rc = validate_interval(c, lo, hi, kinds);
     if (rc) return rc;
     if (c->server_running()) return fail(BNX_E_STATE, "the serving loop owns the context");
@@ -673,6 +868,22 @@ int bnx_search(bnx_ctx *c, uint64_t lo, uint64_t hi, uint32_t kinds, bnx_pair *o
     if ((rc = ensure_ws(c, t, 1))) return rc;
     c->h_ivs[0] = iv;
     return search_staged(c, 1, out, cap, n_out, nullptr);
+}
+
+extern "C" {
+
+int bnx_search(bnx_ctx *c, uint64_t lo, uint64_t hi, uint32_t kinds, bnx_pair *out, size_t cap, size_t *n_out) {
+    if (!c) return fail(BNX_E_ARG, "NULL context");
+    return search_one(c, lo, hi, kinds, out, cap, n_out);
+}
+
+int bnx_search_segment(bnx_ctx *c, uint64_t lo, uint32_t len, uint32_t kinds, bnx_pair *out, size_t cap,
+                       size_t *n_out) {
+    if (!c) return fail(BNX_E_ARG, "NULL context");
+    // (lo > max_hi - len, not lo + len > max_hi: the sum could wrap)
+    if (len < 1 || lo < 1 || len > c->max_hi || lo > c->max_hi - len)
+        return fail(BNX_E_ARG, "need len >= 1, lo >= 1 and lo + len <= max_hi");
+    return search_one(c, lo, lo + len, kinds, out, cap, n_out);
 }
 
 int bnx_batch(bnx_ctx *c, const bnx_interval *ivs, size_t k, bnx_pair *out, size_t cap, size_t *n_out,
@@ -691,9 +902,7 @@ int bnx_batch(bnx_ctx *c, const bnx_interval *ivs, size_t k, bnx_pair *out, size
     if (c->server_running()) return fail(BNX_E_STATE, "the serving loop owns the context");
     std::lock_guard<std::mutex> g(c->mu);
     cudaSetDevice(c->device);
-    PlanTotals t0;
-    t0.segs = t0.chunks = t0.buckets = 0;
-    int rc = ensure_ws(c, t0, k);
+    int rc = ensure_staging(c, k);
     if (rc) return rc;
     for (size_t i = 0; i < k; i++) {
         IvDev &d = c->h_ivs[i];

@@ -20,7 +20,10 @@
 // Host code must not pass the array's name to a kernel (on the host it names a
 // stand-in, not device memory), so the device address is taken once per device
 // with cudaGetSymbolAddress, with that device current, on the first call made
-// on it.  Make that first call before any stream capture begins.
+// on it.  Make that first call before any stream capture begins.  The address
+// is kept per device ordinal for the life of the process: it belongs to the
+// device's primary context, and after cudaDeviceReset (or under another
+// context current on the device) it would be stale.
 #include <cmath>
 #include <cstdint>
 #include <mutex>
@@ -103,7 +106,8 @@ using namespace bnx;
 extern "C" int bnx_rad_segment_noalloc(uint64_t lo, uint64_t len, uint64_t *rad_out, uint64_t *sq_out,
                                        void *stream) {
     if (!rad_out) return fail(BNX_E_ARG, "rad_out is NULL");
-    if (lo < 1 || len < 1 || len > kNaMaxLen || lo + len > kNaMaxHi)
+    // (lo > max - len, not lo + len > max: the sum could wrap)
+    if (lo < 1 || len < 1 || len > kNaMaxLen || lo > kNaMaxHi - len)
         return fail(BNX_E_ARG, "need 1 <= lo, 1 <= len <= %llu and lo + len <= %llu (the fixed scratch limits)",
                     (unsigned long long)kNaMaxLen, (unsigned long long)kNaMaxHi);
     int dev = 0;

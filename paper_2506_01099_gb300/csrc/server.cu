@@ -1,16 +1,23 @@
 // Serving loop (continuous batching of interval requests) and the autotuner.
 //
 // Serving: a host thread owns the context while it runs.  Every iteration it
-//   1. admits waiting requests while a slot is free and the workspace their
-//      next slice needs fits the memory budget (free HBM by default);
+//   1. admits waiting requests (first come, first served) while a slot is free
+//      and the workspace of an iteration that gives every admitted request a
+//      slice of `slice` integers fits the memory budget; a request that does
+//      not fit waits for memory (and is counted once as deferred);
 //   2. cuts the next slice of every active request and runs all slices as one
 //      batched pipeline (one persistent sieve launch over the shared queue), so
 //      the work of requests that arrived at different times overlaps on the GPU.
 //      An iteration covers up to slice * max_active integers, shared equally by the
 //      active requests (at least `slice` each): a request that runs alone or with
-//      few others advances in long slices, and with a full set each gets `slice`;
+//      few others advances in long slices, and with a full set each gets `slice`.
+//      The slices are shortened (down to one queue segment) until the iteration's
+//      workspace fits the budget, and the workspace is sized under the same budget,
+//      so the budget bounds the device memory the loop holds;
 //   3. appends each slice's pairs to its request and retires finished requests.
-// Results are exact, so a request's pairs are the same alone and in any mix.
+// The workspace bytes of an iteration come from the same function that sizes the
+// workspace (ws_need_bytes), so admission and allocation agree.  Results are
+// exact, so a request's pairs are the same alone and in any mix.
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
@@ -35,13 +42,13 @@ struct Request {
     std::vector<bnx_pair> pairs;
     Clock::time_point t_submit, t_done;
     bool done = false;
+    bool deferred = false;  // waited for memory at least once
     int status = BNX_OK;
-    uint64_t reserved = 0;
 };
 
 struct Server {
     bnx_server_cfg cfg{};
-    uint64_t budget = 0, reserved = 0;
+    uint64_t budget = 0;
     std::thread th;
     std::mutex m;
     std::condition_variable cv;
@@ -52,13 +59,31 @@ struct Server {
     std::unordered_map<uint64_t, std::shared_ptr<Request>> all;
     std::vector<bnx_pair> buf;
     std::vector<uint64_t> offs;
+    std::vector<IvDev> plan_tmp;
+    bnx_server_stats st{};
 };
 
-// Device bytes one slice of a request needs in the shared workspace.
-static uint64_t slice_bytes(bnx_ctx *c, uint64_t lo, uint64_t hi) {
-    const uint64_t ns = ((hi - lo) >> c->seg_log2()) + 1;
-    return bucket_bound(c, lo, hi, ns) * sizeof(uint2) + ns * (sizeof(uint32_t) + sizeof(unsigned long long)) +
-           sizeof(IvDev) + 64;
+// End of a request's next slice of `per` integers (no overflow for any per).
+static uint64_t slice_end(const Request &r, uint64_t per) {
+    return per >= r.iv.hi - r.cursor ? r.iv.hi : r.cursor + per;
+}
+
+// Workspace bytes of an iteration in which each request runs its next `per` integers.
+static uint64_t iteration_bytes(bnx_ctx *c, const std::vector<std::shared_ptr<Request>> &rs, uint64_t per,
+                                std::vector<IvDev> &tmp) {
+    tmp.assign(rs.size(), IvDev{});
+    for (size_t i = 0; i < rs.size(); i++) {
+        tmp[i].lo = rs[i]->cursor;
+        tmp[i].hi = slice_end(*rs[i], per);
+    }
+    PlanTotals t;
+    plan_host(c, tmp.data(), rs.size(), &t);
+    return ws_need_bytes(c, t, rs.size());
+}
+
+static void publish_stats(bnx_ctx *c, const Server &S) {
+    std::lock_guard<std::mutex> g(c->stats_mu);
+    c->srv_stats = S.st;
 }
 
 static void serve(bnx_ctx *c) {
@@ -71,14 +96,28 @@ static void serve(bnx_ctx *c) {
             if (S.stop) break;
             while (!S.pending.empty() && S.active.size() < S.cfg.max_active) {
                 auto r = S.pending.front();
-                const uint64_t hi = std::min(r->iv.hi, r->cursor + S.cfg.slice);
-                const uint64_t need = slice_bytes(c, r->cursor, hi);
-                if (S.reserved + need > S.budget && !S.active.empty()) break;  // wait for memory
-                r->reserved = need;
-                S.reserved += need;
+                auto trial = S.active;
+                trial.push_back(r);
+                if (iteration_bytes(c, trial, S.cfg.slice, S.plan_tmp) > S.budget) {
+                    if (S.active.empty()) {  // its first slice does not fit even alone: it never will
+                        r->status = BNX_E_NOMEM;
+                        r->done = true;
+                        r->t_done = Clock::now();
+                        S.pending.pop_front();
+                        S.st.rejected++;
+                        S.st.completed++;
+                        continue;
+                    }
+                    if (!r->deferred) {
+                        r->deferred = true;
+                        S.st.deferred++;
+                    }
+                    break;  // wait for memory: first come, first served
+                }
                 S.active.push_back(r);
                 S.pending.pop_front();
             }
+            publish_stats(c, S);
             if (S.active.empty()) {
                 S.cv.wait_for(lk, std::chrono::milliseconds(50));
                 continue;
@@ -86,30 +125,34 @@ static void serve(bnx_ctx *c) {
             batch = S.active;
         }
         const size_t k = batch.size();
-        // this iteration's slice: an equal share of slice * max_active, at least `slice`
-        const uint64_t budget = S.cfg.slice > UINT64_MAX / S.cfg.max_active ? UINT64_MAX : S.cfg.slice * S.cfg.max_active;
-        const uint64_t per = std::max<uint64_t>(S.cfg.slice, budget / k);
-        PlanTotals t0{0, 0, 0, 0};
-        int rc = ensure_ws(c, t0, k);
+        // this iteration's slice: an equal share of slice * max_active, at least `slice`,
+        // shortened while the iteration's workspace exceeds the budget
+        const uint64_t share = S.cfg.slice > UINT64_MAX / S.cfg.max_active ? UINT64_MAX : S.cfg.slice * S.cfg.max_active;
+        const uint64_t seg = 1ull << c->seg_log2();
+        uint64_t per = std::max<uint64_t>(S.cfg.slice, share / k);
+        while (per > seg && iteration_bytes(c, batch, per, S.plan_tmp) > S.budget) per = std::max(seg, per / 2);
+        int rc = ensure_staging(c, k);
         if (rc == BNX_OK) {
             for (size_t i = 0; i < k; i++) {
                 const Request &r = *batch[i];
                 IvDev &d = c->h_ivs[i];
                 memset(&d, 0, sizeof d);
                 d.lo = r.cursor;
-                d.hi = std::min(r.iv.hi, r.cursor + per);
+                d.hi = slice_end(r, per);
                 d.kinds = r.iv.kinds;
                 d.id = (uint32_t)i;
             }
             S.offs.assign(k + 1, 0);
             size_t np = 0;
-            rc = search_staged(c, k, S.buf.data(), S.buf.size(), &np, S.offs.data());
+            rc = search_staged(c, k, S.buf.data(), S.buf.size(), &np, S.offs.data(), S.budget);
             if (rc == BNX_E_TRUNCATED) {
                 S.buf.resize(np + 64);
-                rc = search_staged(c, k, S.buf.data(), S.buf.size(), &np, S.offs.data());
+                rc = search_staged(c, k, S.buf.data(), S.buf.size(), &np, S.offs.data(), S.budget);
             }
         }
         std::lock_guard<std::mutex> lk(S.m);
+        S.st.iterations++;
+        S.st.ws_peak_bytes = std::max<uint64_t>(S.st.ws_peak_bytes, ws_footprint(c));
         std::vector<std::shared_ptr<Request>> still;
         for (size_t i = 0; i < k; i++) {
             Request &r = *batch[i];
@@ -119,7 +162,7 @@ static void serve(bnx_ctx *c) {
                     p.iv = r.iv.id;
                     r.pairs.push_back(p);
                 }
-                r.cursor = std::min(r.iv.hi, r.cursor + per);
+                r.cursor = slice_end(r, per);
             } else {
                 r.status = rc;
                 r.cursor = r.iv.hi;
@@ -127,7 +170,7 @@ static void serve(bnx_ctx *c) {
             if (r.cursor >= r.iv.hi) {
                 r.done = true;
                 r.t_done = Clock::now();
-                S.reserved -= r.reserved;
+                S.st.completed++;
             } else {
                 still.push_back(batch[i]);
             }
@@ -135,6 +178,7 @@ static void serve(bnx_ctx *c) {
         // requests admitted during this iteration are appended after `batch`
         for (size_t i = k; i < S.active.size(); i++) still.push_back(S.active[i]);
         S.active.swap(still);
+        publish_stats(c, S);
     }
 }
 
@@ -147,6 +191,7 @@ extern "C" {
 int bnx_server_start(bnx_ctx *c, const bnx_server_cfg *cfg) {
     if (!c || !cfg) return fail(BNX_E_ARG, "NULL argument");
     if (cfg->max_active < 1 || cfg->slice < 1) return fail(BNX_E_ARG, "max_active and slice must be >= 1");
+    if (cfg->max_active > (1u << 24)) return fail(BNX_E_ARG, "max_active must be <= 2^24 (a batch's interval limit)");
     std::lock_guard<std::mutex> g(c->mu);
     if (c->serving.load()) return fail(BNX_E_STATE, "already serving");
     cudaSetDevice(c->device);
@@ -164,6 +209,7 @@ int bnx_server_start(bnx_ctx *c, const bnx_server_cfg *cfg) {
         }
         S->budget = (uint64_t)(0.9 * (double)fr);
     }
+    S->st.budget_bytes = S->budget;
     S->buf.resize(4096);
     c->server = S;
     c->serving.store(true);
@@ -186,6 +232,8 @@ int bnx_server_submit(bnx_ctx *c, const bnx_interval *iv, uint64_t *ticket) {
         r->ticket = S.next_ticket++;
         S.pending.push_back(r);
         S.all[r->ticket] = r;
+        S.st.submitted++;
+        publish_stats(c, S);
     }
     S.cv.notify_one();
     *ticket = r->ticket;
@@ -229,6 +277,31 @@ int bnx_server_stop(bnx_ctx *c) {
     c->serving.store(false);
     c->server = nullptr;
     delete S;
+    return BNX_OK;
+}
+
+int bnx_server_get_stats(bnx_ctx *c, bnx_server_stats *out) {
+    if (!c || !out) return fail(BNX_E_ARG, "NULL argument");
+    std::lock_guard<std::mutex> g(c->stats_mu);
+    *out = c->srv_stats;
+    return BNX_OK;
+}
+
+int bnx_workspace_bytes(bnx_ctx *c, const bnx_interval *iv, size_t k, uint64_t *bytes) {
+    if (!c || !bytes || (!iv && k)) return fail(BNX_E_ARG, "NULL argument");
+    if (k > (1u << 24)) return fail(BNX_E_ARG, "at most 2^24 intervals per batch");
+    std::vector<IvDev> d(k);
+    for (size_t i = 0; i < k; i++) {
+        int rc = validate_interval(c, iv[i].lo, iv[i].hi, iv[i].kinds);
+        if (rc) return rc;
+        memset(&d[i], 0, sizeof d[i]);
+        d[i].lo = iv[i].lo;
+        d[i].hi = iv[i].hi;
+    }
+    std::lock_guard<std::mutex> g(c->mu);
+    PlanTotals t;
+    plan_host(c, d.data(), k, &t);
+    *bytes = ws_need_bytes(c, t, k);
     return BNX_OK;
 }
 

@@ -1,10 +1,11 @@
 // Log-domain tile sieve for the search and hash modes (the default).
 //
-// The tile holds, per value x, L(x) = the sum of lg(p) over the prime-power
-// strikes at x, where lg(p) = floor(F log2 p) + 1 > F log2 p in the tile's
-// fixed-point scale F (2^16 for u32 values, 2^8 for u16, 2 for u8).  So L(x) is
-// an upper bound of F log2 s_odd(x), s_odd(x) being the odd part of
-// x / rad(x).  Strikes are 32-bit shared-memory reductions (no read-modify-write
+// The tile holds, per value x, L(x) = the sum of w(p) over the prime-power
+// strikes at x, where w(p) >= F log2 p in the tile's fixed-point scale F (2^16
+// for u32 values, 2^8 for u16, 2 for u8): the weights of bnx_internal.cuh, the
+// bit length of p^F computed in integers (no floating point decides anything
+// here).  So L(x) is an upper bound of F log2 s_odd(x), s_odd(x) being the odd
+// part of x / rad(x).  Strikes are 32-bit shared-memory reductions (no read-modify-write
 // loop: addition commutes, so strikes of different prime powers at one x need
 // no ordering).  Algorithm 1 (Sec. 2.1) still decides which x a prime power
 // touches; only what is recorded there changes.
@@ -20,6 +21,8 @@
 // dropped; the rest go to a list that k_cand (below) checks with exact square
 // parts (exact-division tests by the in-tile primes, plus the segment's bucket
 // entries of the larger primes) and the exact 128-bit conditions.
+#include <algorithm>
+
 #include "bnx_internal.cuh"
 
 namespace bnx {
@@ -28,13 +31,13 @@ namespace {
 
 // The first 512 bucket entries of a segment (a segment of 2^19 values near 2^40
 // holds about 370 at Q = 2^16) are cached in shared memory, each packed into one
-// word: (offset in the segment) << 12 | lg7, lg7 = ceil(log2 p * 2^7) with
-// margin (p < 2^22: lg7 < 2^12).  Offsets reach the segment length, so the
-// cache is used for segments of at most 2^19 values; the entries of larger
-// segments, and those beyond the cache, are read from global memory.  A strike
-// adds lg7 << 9 to the u32 tile (units 2^-16), lg7 << 1 to the u16 tile (units
-// 2^-8) or ceil(lg7 / 2^6) to the u8 tile (units 2^-1): an over-estimate of
-// log2 p, as the rejection rule needs.
+// word: (offset in the segment) << 12 | cache_weight(p) (below 2^12 for
+// p < 2^21).  Offsets reach the segment length, so the cache is used for
+// segments of at most 2^19 values; the entries of larger segments, and those
+// beyond the cache, are read from global memory.  Either way a strike adds
+// bucket_weight(p) -- the u8 tile's own weight, or the weight in units of 2^-7
+// scaled by 2 (u16 tile) or 2^9 (u32 tile) -- an over-estimate of F log2 p, as
+// the rejection rule needs.
 constexpr int kLogBucketCache = 512;
 // The cached entries are then binned by tile (bsort), so that a tile reads only its own;
 // an entry on a tile boundary (x = L_tile of one tile, x = 0 of the next) is in both bins.
@@ -74,15 +77,11 @@ __host__ __device__ inline LogLayout log_layout(uint32_t tile_log2, uint32_t nsp
     return L;
 }
 
-// lg of a large prime for a bucket hit: 2^16 log2 p rounded up with margin
-// (log2f is within a few ulps; 4 units of 2^-16 cover that and the truncation)
-__device__ __forceinline__ uint32_t lg_large(uint32_t p) {
-    return __float2uint_rd(log2f((float)p) * 65536.0f) + 4u;
+// a bucket entry packed for the shared cache: its offset and its weight field
+template <int VB>
+__device__ __forceinline__ uint32_t pack_hit(uint2 h) {
+    return (h.x << 12) | cache_weight<VB>(h.y);
 }
-// the same in units of 2^-8 (u16 tile); 2 units cover the error and the truncation
-__device__ __forceinline__ uint32_t lg_large8(uint32_t p) { return __float2uint_rd(log2f((float)p) * 256.0f) + 2u; }
-// a bucket entry packed for the shared cache (units of 2^-7, rounded up from lg_large8)
-__device__ __forceinline__ uint32_t pack_hit(uint2 h) { return (h.x << 12) | ((lg_large8(h.y) + 1u) >> 1); }
 
 struct SmallPrimes {
     uint32_t n;
@@ -148,9 +147,9 @@ struct LogMinBlocks {
 //    L(x) <= 2^8 log2 s_odd(x) + (strikes at x) < 42 * 2^8 + 42 < 2^14, and a pair sum
 //    L(n) + L(n+1) < 2^15, so a strike's addition of lg << 16*(x&1) never carries into
 //    the neighbour, nor does a pair sum.
-//  VB = 1: 8 bits with 1 fractional bit (half-bit units), four values per word.  lg(p)
+//  VB = 1: 8 bits with 1 fractional bit (half-bit units), four values per word.  w(p)
 //    = floor(2 log2 p) + 1 is at most 4/log2(3) = 2.52 units per bit of p (p = 3 is the
-//    worst; a bucket prime p > 2^7 takes at most 2 + 2/7 units per bit), so for x < 2^42
+//    worst; a prime p > 2^7 takes at most 2 + 1/7 units per bit), so for x < 2^42
 //    L(x) <= 2.52 * 41 < 2^7 and a pair sum L(n) + L(n+1) <= 2.52 * 84 < 2^8: neither a
 //    strike nor a pair sum carries into the neighbouring byte.
 template <int MODE, int NT, int VB>
@@ -201,14 +200,14 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
     __shared__ uint4 s_pat[kPat ? 81 : 1];
     for (uint32_t j = tid; j < nspp; j += NT) {
         const SmallPP e = P.spp[j];
-        const uint32_t lg = VB == 4 ? e.lg : (uint32_t)floor(log2((double)e.p) * (double)FS) + 1u;
+        const uint32_t lg = tile_weight<VB>(e.p);
         const bool in_pat = kPat && (e.q == 9 || e.q == 27 || e.q == 81);
         // rounds: at most floor(L_tile/q)+1 multiples of q per tile; 0 = not in the schedule
         sdesc[j] = make_uint4(e.q, lg, 0u, in_pat ? 0u : (LT / e.q + 1 + 31) / 32);
         slmod[j] = LT % e.q;
     }
     if (kPat && tid < 81) {
-        const uint32_t lg3 = (uint32_t)floor(log2(3.0) * (double)FS) + 1u;
+        const uint32_t lg3 = tile_weight<VB>(3);
         uint32_t w[4] = {0, 0, 0, 0};
         for (uint32_t c = 0; c < 4; c++)
             for (uint32_t b = 0; b < 4; b++) {
@@ -320,7 +319,7 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
         }
         const uint32_t ntl = (seg_len + LT - 1) >> tile_log2;  // tiles of this segment (<= kMaxSegTiles)
         for (uint32_t e = tid; e < nbc; e += NT) {
-            const uint32_t w = pack_hit(P.bent[b0 + e]);
+            const uint32_t w = pack_hit<VB>(P.bent[b0 + e]);
             bcache[e] = w;
             const uint32_t o = w >> 12, t1 = o >> tile_log2;
             if (t1 < ntl) atomicAdd(&s_bcnt[t1], 1u);
@@ -442,8 +441,7 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
                 const uint32_t w = bsort[e];
                 const uint32_t x = (w >> 12) - t0;
                 if (x <= tl) {
-                    const uint32_t lg7 = w & 0xfffu;
-                    const uint32_t lg = VB == 4 ? lg7 << 9 : VB == 2 ? lg7 << 1 : (lg7 + 63u) >> 6;
+                    const uint32_t lg = cache_to_tile<VB>(w & 0xfffu);
                     red_add_shared(tile_s + ((x >> VSH) << 2), lg << ((x & (VPW - 1)) * VBITS));
                 }
             }
@@ -451,7 +449,7 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
                 const uint2 h = P.bent[e];
                 if (h.x >= t0 && h.x <= t0 + tl) {
                     const uint32_t x = h.x - t0;
-                    const uint32_t lg = VB == 4 ? lg_large(h.y) : VB == 2 ? lg_large8(h.y) : (lg_large8(h.y) + 127u) >> 7;
+                    const uint32_t lg = bucket_weight<VB>(h.y);
                     atomicAdd(&tile[x >> VSH], lg << ((x & (VPW - 1)) * VBITS));
                 }
             }
@@ -678,7 +676,29 @@ const void *log_fn(int mode, int threads, int vb) {
     return mode == kModeHash ? log_fn_m<kModeHash>(threads, vb) : log_fn_m<kModeSearch>(threads, vb);
 }
 
+// The weights a log tile of VB bytes per value adds for each prime of the table,
+// taken along the kernel's own paths: out[4i .. 4i+4) = {p, in-tile strike weight,
+// weight of a bucket hit through the shared cache (packed and unpacked as the
+// sieve does), weight of a bucket hit read from global memory}.
+template <int VB>
+__global__ void k_log_weights(const uint32_t *primes, uint32_t np, uint32_t *out) {
+    for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
+        const uint32_t p = primes[i];
+        out[4 * (size_t)i] = p;
+        out[4 * (size_t)i + 1] = tile_weight<VB>(p);
+        out[4 * (size_t)i + 2] = cache_to_tile<VB>(pack_hit<VB>(make_uint2(0u, p)) & 0xfffu);
+        out[4 * (size_t)i + 3] = bucket_weight<VB>(p);
+    }
+}
+
 }  // namespace
+
+void launch_log_weights(const uint32_t *primes, uint32_t np, int vb, uint32_t *out, cudaStream_t s) {
+    const int grid = (int)std::min<uint32_t>((np + 255) / 256 + 1, 1024u);
+    if (vb == 1) k_log_weights<1><<<grid, 256, 0, s>>>(primes, np, out);
+    else if (vb == 2) k_log_weights<2><<<grid, 256, 0, s>>>(primes, np, out);
+    else k_log_weights<4><<<grid, 256, 0, s>>>(primes, np, out);
+}
 
 size_t sieve_log_smem_bytes(uint32_t tile_log2, uint32_t nspp, uint32_t nsched, int vb) {
     return log_layout(tile_log2, nspp, nsched, vb).total;

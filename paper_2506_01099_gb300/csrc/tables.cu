@@ -107,7 +107,7 @@ __global__ void k_pp_write(const uint32_t *primes, uint32_t np, uint64_t max_hi,
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < np; i += gridDim.x * blockDim.x) {
         const uint64_t p = primes[i];
         if (p == 2 || p * p > max_hi) continue;
-        const uint32_t lg = (uint32_t)floor(log2((double)p) * (double)(1u << kLogFrac)) + 1u;
+        const uint32_t lg = log_weight(p, kLogFrac);
         uint32_t si = os[i], li = ol[i], e = 2;
         for (uint64_t q = p * p;; q *= p, e++) {
             if (q <= q_small) {

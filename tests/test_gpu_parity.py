@@ -361,3 +361,200 @@ def test_algorithm2_sorted_bad_arguments(B, ctx):
         with pytest.raises(B.BnxError) as e:
             ctx.search_sorted(S, kinds)
         assert e.value.code == B.BNX_E_ARG
+
+
+SEGMENT_CASES = [
+    (1, 1 << 20),                         # from 1: the small pairs, (2, 3) first
+    (2**32 - 2**19 - 17, 2**20 + 33),     # across 2^32, ragged
+    (2**40 - 2**21, 2**21),               # ends at 2^40
+    (2**40, 2**21 + 1),                   # starts at 2^40: holds (2^20 + 1, 2^40 + 2^21)
+    (MAX_HI - 2**20, 2**20),              # ends at the context's max_hi
+]
+
+
+@pytest.mark.parametrize("lo,length", SEGMENT_CASES)
+def test_search_segment_vs_oracle(ctx, orc, lo, length):
+    """bnx_search_segment (Algorithm 3's output for one chunk) equals the oracle."""
+    got = ctx.search_segment(lo, length)
+    assert got == orc.pairs_crt(lo, lo + length)
+    st = ctx.stats()
+    assert (st["survivors1"], st["survivors2"]) == orc.filter_counts(lo, lo + length)
+
+
+def test_search_segment_straddles_family_members(ctx):
+    """Segments that start, end or sit on every pair member of Theorem 1 below 2^40."""
+    for m, n, kind in theorem1_pairs(1, 1 << 40):
+        for lo, length in ((n, 1), (max(1, n - 999), 1000), (max(1, n - 500), 1001), (n + 1, 4096)):
+            assert ctx.search_segment(lo, length) == theorem1_pairs(lo, lo + length), (lo, length)
+        assert ctx.search_segment(n, 1, 3 - kind) == theorem1_pairs(n, n + 1, 3 - kind)  # n = 8 has both kinds
+
+
+def test_segment_loop_equals_search(ctx):
+    """A caller's own loop of consecutive segments concatenates to bnx_search's result."""
+    lo, hi = 2**40 - 2**22 - 5, 2**40 + 2**22 + 12345
+    step = (1 << 20) + 7
+    got = []
+    for a in range(lo, hi, step):
+        got += ctx.search_segment(a, min(step, hi - a))
+    assert got == ctx.search(lo, hi) == theorem1_pairs(lo, hi)
+
+
+def test_search_segment_bad_arguments(B, ctx):
+    import ctypes
+
+    L = B.lib()
+    n = ctypes.c_size_t()
+    for lo, length, kinds in ((0, 10, 3), (1, 0, 3), (MAX_HI - 9, 10, 3), (2**64 - 1, 2, 3), (2**64 - 5, 10, 3),
+                              (1, 10, 0), (1, 10, 8)):
+        assert L.bnx_search_segment(ctx.h, lo, length, kinds, None, 0, ctypes.byref(n)) == B.BNX_E_ARG, (lo, length)
+    assert L.bnx_search_segment(ctx.h, MAX_HI - 10, 10, 3, None, 0, ctypes.byref(n)) == B.BNX_OK
+    with B.Context(0, max_hi=1 << 20) as small:  # len beyond max_hi must not wrap the check
+        assert L.bnx_search_segment(small.h, 1, 1 << 30, 3, None, 0, ctypes.byref(n)) == B.BNX_E_ARG
+
+
+def test_rad_segment_host_buffers(ctx, orc):
+    """bnx_rad_segment into HOST buffers (pageable numpy arrays): the same values as into
+    device buffers, and the oracle's trial-division radicals."""
+    for lo, length in ((2**40 - 2**13, 2**14 + 3), (1, 70_000)):
+        rad = np.zeros(length, dtype=np.uint64)
+        sq = np.zeros(length, dtype=np.uint64)
+        ctx.rad_segment(lo, length, rad.ctypes.data, sq.ctypes.data, None)
+        drad, dsq = gpu_rad(ctx, lo, length)
+        assert np.array_equal(rad, drad) and np.array_equal(sq, dsq)
+        assert np.array_equal(rad, orc.rad_td_array(lo, length))
+        rad_only = np.zeros(length, dtype=np.uint64)
+        ctx.rad_segment(lo, length, rad_only.ctypes.data, None, None)
+        assert np.array_equal(rad_only, rad)
+
+
+def test_rad_segment_bad_arguments(B, ctx):
+    import ctypes
+
+    import torch
+
+    L = B.lib()
+    dev = torch.empty(16, dtype=torch.int64, device="cuda")
+    host = np.zeros(16, dtype=np.uint64)
+    for lo, length in ((0, 4), (1, 0), (2**64 - 1, 2), (2**64 - 8, 16), (MAX_HI - 3, 4), (1, (1 << 31) + 1)):
+        assert L.bnx_rad_segment(ctx.h, lo, length, dev.data_ptr(), None, None) == B.BNX_E_ARG, (lo, length)
+    # rad and sq must both be host or both device buffers
+    assert L.bnx_rad_segment(ctx.h, 5, 16, dev.data_ptr(), host.ctypes.data, None) == B.BNX_E_ARG
+    assert L.bnx_rad_segment(ctx.h, 5, 16, None, None, None) == B.BNX_E_ARG
+    torch.cuda.synchronize()
+
+
+def test_algorithm2_lookback_wait_runs_out(B, ctx, orc):
+    """The radix sort's bounded look-back wait: with the test hook, tile 0 of the first
+    pass withholds its counts, the waits on it give up after 1024 polls, and the call
+    fails with BNX_E_TIMEOUT instead of stalling; the next call is clean."""
+    import ctypes
+
+    L = B.lib()
+    assert L.bnx_arm_lookback_timeout(ctx.h, 0) == B.BNX_E_ARG
+    assert L.bnx_arm_lookback_timeout(ctx.h, (1 << 22) + 1) == B.BNX_E_ARG
+    S = 1 << 16  # 10 sort tiles
+    B.bnx_arm_lookback_timeout(ctx.h, 1024)
+    n = ctypes.c_size_t(12345)
+    assert L.bnx_search_sorted(ctx.h, S, 3, None, 0, ctypes.byref(n)) == B.BNX_E_TIMEOUT
+    assert "look-back" in B.bnx_last_error()
+    assert ctx.search_sorted(S) == orc.pairs_sort(S)  # disarmed
+    assert ctx.search(1, 1 << 20) == theorem1_pairs(1, 1 << 20)
+
+
+def test_server_admission_by_memory(B, orc):
+    """A workspace budget that holds one request's slice but not two: the second and
+    third requests wait for memory (first come, first served), the workspace never
+    exceeds the budget, and every request's pairs equal its result alone, Theorem 1 and
+    the oracle."""
+    import time
+
+    sl = 1 << 30
+    base = 1 << 40
+    reqs = [(base + i * 2 * sl, base + (i + 1) * 2 * sl, 3) for i in range(3)]
+    with B.Context(0, max_hi=MAX_HI) as c:
+        one = B.bnx_workspace_bytes(c.h, [(reqs[0][0], reqs[0][0] + sl, 3)])
+        two = B.bnx_workspace_bytes(c.h, [(r[0], r[0] + sl, 3) for r in reqs[:2]])
+        assert two > one > 0
+        budget = (one + two) // 2
+        alone = [c.search(*r) for r in reqs]
+        B.bnx_server_start(c.h, max_active=4, slice_len=sl, mem_budget=budget)
+        try:
+            tickets = [B.bnx_server_submit(c.h, *r) for r in reqs]
+            got = {}
+            t0 = time.time()
+            while len(got) < len(tickets) and time.time() - t0 < 300:
+                for t in tickets:
+                    if t not in got:
+                        r = B.bnx_server_poll(c.h, t)
+                        if r is not None:
+                            got[t] = r
+                time.sleep(0.002)
+        finally:
+            B.bnx_server_stop(c.h)
+        st = B.bnx_server_get_stats(c.h)
+    assert len(got) == 3
+    assert st["submitted"] == 3 and st["completed"] == 3 and st["rejected"] == 0
+    assert st["deferred"] == 2, st  # the second and the third request waited for memory
+    assert st["budget_bytes"] == budget and 0 < st["ws_peak_bytes"] <= budget, st
+    assert st["iterations"] >= 6  # slices shortened to fit: 2^30 integers per iteration
+    lat = [got[t][1] for t in tickets]
+    assert lat[0] < lat[1] < lat[2]  # one after the other
+    for t, r, want in zip(tickets, reqs, alone):
+        assert got[t][0] == want == theorem1_pairs(r[0], r[1]) == orc.pairs_crt(r[0], r[1])
+    assert alone[0] == [(1048577, 1099513724928, 2)]
+
+
+def test_server_rejects_a_request_that_never_fits(B):
+    """A budget below one slice's workspace: the request finishes at once with BNX_E_NOMEM."""
+    import time
+
+    with B.Context(0, max_hi=MAX_HI) as c:
+        need = B.bnx_workspace_bytes(c.h, [(1 << 40, (1 << 40) + (1 << 26), 3)])
+        B.bnx_server_start(c.h, max_active=2, slice_len=1 << 26, mem_budget=need // 2)
+        try:
+            t = B.bnx_server_submit(c.h, 1 << 40, (1 << 40) + (1 << 26), 3)
+            t0 = time.time()
+            while time.time() - t0 < 60:
+                try:
+                    r = B.bnx_server_poll(c.h, t)
+                except B.BnxError as e:
+                    assert e.code == B.BNX_E_NOMEM
+                    break
+                assert r is None
+                time.sleep(0.002)
+            else:
+                raise AssertionError("no answer")
+        finally:
+            B.bnx_server_stop(c.h)
+        st = B.bnx_server_get_stats(c.h)
+    assert st["rejected"] == 1 and st["iterations"] == 0
+
+
+def test_autotune_picks_a_sound_tuning(B, orc):
+    """bnx_autotune over 64 intervals of the batched workload (one timed round per
+    candidate): the JSON it returns parses, every field lies in its search space, the
+    context keeps that tuning, and searches with it equal Theorem 1 and the oracle
+    (pairs and survivor counts)."""
+    import json
+
+    from paper_2506_01099_gb300 import workloads as W
+
+    ivs = [iv for iv in W.batch_intervals(4096) if iv.length <= (1 << 26)][:64]
+    with B.Context(0, max_hi=MAX_HI) as c:
+        text = c.autotune(ivs, rounds=1)
+        d = json.loads(text)
+        assert set(d) == {"tile_log2", "seg_tiles", "threads", "ctas_per_sm", "small_q_log2", "tile_kind", "ms"}
+        assert d["tile_log2"] in (13, 14, 15, 16) and d["seg_tiles"] in (2, 4, 8, 16, 32)
+        assert d["threads"] in (128, 256, 512, 1024) and d["small_q_log2"] in (12, 13, 14, 15, 16)
+        assert d["ctas_per_sm"] in (0, 1, 2) and d["tile_kind"] in (0, 2, 3) and d["ms"] > 0
+        tuned = c.tune()
+        assert tuned == {k: v for k, v in d.items() if k != "ms"}
+        assert B.bnx_tune_parse(text).as_dict() == tuned
+        assert c.search(1, 1 << 20) == theorem1_pairs(1, 1 << 20)
+        lo = 1 << 40
+        assert c.search(lo, lo + (1 << 21)) == orc.pairs_crt(lo, lo + (1 << 21))
+        st = c.stats()
+        assert (st["survivors1"], st["survivors2"]) == orc.filter_counts(lo, lo + (1 << 21))
+        pairs, offs = c.batch(ivs)
+        for i, iv in enumerate(ivs):
+            assert [(m, n, kd) for (_, m, n, kd) in pairs[offs[i]:offs[i + 1]]] == theorem1_pairs(iv.lo, iv.hi, iv.kinds)
