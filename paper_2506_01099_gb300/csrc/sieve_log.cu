@@ -375,12 +375,13 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
                 if constexpr (kPat) {
                     // word w of the tile starts at n = t_lo + 4w: store i (words 4i ..) starts at
                     // t_lo + 16 i, whose entry is r' = (t_lo + 16 i) / 16 mod 81 = 76 t_lo + i
-                    // (16 * 76 = 1 mod 81)
-                    constexpr uint32_t kStep = NT % 81u;
-                    uint32_t r = (uint32_t)((t_lo * 76ull + tid) % 81ull);
-                    for (uint32_t i = tid; i < n4; i += NT) {
-                        t4[i] = s_pat[r];
-                        r = r + kStep >= 81 ? r + kStep - 81 : r + kStep;
+                    // (16 * 76 = 1 mod 81).  Thread t < NS (NS the largest multiple of 81 not above
+                    // NT) makes the stores i = t mod NS, which all take the same entry 76 t_lo + t
+                    // mod 81: one table load per tile, then plain 16-byte stores.
+                    constexpr uint32_t NS = NT / 81u * 81u;
+                    if (tid < NS) {
+                        const uint4 e = s_pat[(uint32_t)((t_lo * 76ull + tid) % 81ull)];
+                        for (uint32_t i = tid; i < n4; i += NS) t4[i] = e;
                     }
                 } else {
                     for (uint32_t i = tid; i < n4; i += NT) t4[i] = z;
