@@ -56,6 +56,8 @@ class Oracle:
         for f in ("orc_pairs_brute", "orc_pairs_sort", "orc_pairs_map"):
             getattr(lib, f).argtypes = [u64, u32, ctypes.POINTER(OrcPair), sz]
             getattr(lib, f).restype = sz
+        lib.orc_pairs_brute_rad.argtypes = [ctypes.POINTER(u64), u64, u32, ctypes.POINTER(OrcPair), sz]
+        lib.orc_pairs_brute_rad.restype = sz
         lib.orc_pairs_crt.argtypes = [u64, u64, u32, ctypes.POINTER(OrcPair), sz, i32]
         lib.orc_pairs_crt.restype = sz
         lib.orc_filter_counts.argtypes = [u64, u64, u32, ctypes.POINTER(u64), ctypes.POINTER(u64), i32]
@@ -105,6 +107,16 @@ class Oracle:
     def pairs_brute(self, N: int, kinds: int = 3):
         """All pairs with m < n < N (N <= 2^14), by comparing every m < n."""
         return self._collect(self.lib.orc_pairs_brute, N, kinds)
+
+    def pairs_brute_rad(self, r, N: int, kinds: int = 3):
+        """The definitions of Sec. 1 applied to a given radical array r[0 .. N+1] (r[0]
+        unused; any values), every m < n < N (N <= 2^14)."""
+        import numpy as np
+
+        arr = np.ascontiguousarray(r, dtype=np.uint64)
+        assert arr.size >= N + 2
+        ptr = arr.ctypes.data_as(ctypes.POINTER(ctypes.c_uint64))
+        return self._collect(lambda N_, k_, buf, cap: self.lib.orc_pairs_brute_rad(ptr, N_, k_, buf, cap), N, kinds)
 
     def pairs_sort(self, S: int, kinds: int = 3):
         """All pairs with m < n < S (S <= 2^26), by Algorithm 2 with group-wise pairing."""

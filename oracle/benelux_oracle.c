@@ -219,13 +219,15 @@ static void push_pair(orc_pair *out, size_t cap, size_t *cnt, uint64_t m, uint64
     (*cnt)++;
 }
 
-/* Every 1 <= m < n < N is compared; rad by trial division.  Returns the number
- * of pairs (which may exceed cap; only cap are written).  N <= 2^14. */
-size_t orc_pairs_brute(uint64_t N, uint32_t kinds, orc_pair *out, size_t cap) {
-    if (N < 2 || N > (1u << 14)) return 0;
-    uint64_t *r = (uint64_t *)malloc((N + 2) * sizeof(uint64_t));
-    if (!r) return 0;
-    for (uint64_t x = 1; x <= N + 1; x++) r[x] = orc_rad_td(x);
+/* The definitions of Sec. 1 applied to a given array of radicals r[1 .. N+1]
+ * (r[0] unused): every 1 <= m < n < N is compared, first kind r[m] = r[n] and
+ * r[m+1] = r[n+1], second kind r[m] = r[n+1] and r[m+1] = r[n], three-term a
+ * first-kind pair with also r[m+2] = r[n+2] (Erdos's question, Sec. 1).  The
+ * array may be anything (the tests plant collisions no real radicals give).
+ * Returns the number of pairs (which may exceed cap; only cap are written),
+ * sorted by (n, m, kind).  2 <= N <= 2^14. */
+size_t orc_pairs_brute_rad(const uint64_t *r, uint64_t N, uint32_t kinds, orc_pair *out, size_t cap) {
+    if (!r || N < 2 || N > (1u << 14)) return 0;
     size_t cnt = 0;
     for (uint64_t n = 2; n < N; n++)
         for (uint64_t m = 1; m < n; m++) {
@@ -235,11 +237,27 @@ size_t orc_pairs_brute(uint64_t N, uint32_t kinds, orc_pair *out, size_t cap) {
             if ((kinds & 1) && r[m] == r[n] && r[m + 1] == r[n + 1]) push_pair(out, cap, &cnt, m, n, 1);
 #endif
             if ((kinds & 2) && r[m] == r[n + 1] && r[m + 1] == r[n]) push_pair(out, cap, &cnt, m, n, 2);
+#if ORC_MUTANT == 9 /* mistake: the three-term rule compares m + 2 with n + 1 */
+            if ((kinds & 4) && r[m] == r[n] && r[m + 1] == r[n + 1] && r[m + 2] == r[n + 1])
+#else
             if ((kinds & 4) && r[m] == r[n] && r[m + 1] == r[n + 1] && r[m + 2] == r[n + 2])
+#endif
                 push_pair(out, cap, &cnt, m, n, 4);
         }
-    free(r);
     if (cnt && cnt <= cap) qsort(out, cnt, sizeof(orc_pair), cmp_pair);
+    return cnt;
+}
+
+/* Every 1 <= m < n < N is compared; rad by trial division.  Returns the number
+ * of pairs (which may exceed cap; only cap are written).  N <= 2^14. */
+size_t orc_pairs_brute(uint64_t N, uint32_t kinds, orc_pair *out, size_t cap) {
+    if (N < 2 || N > (1u << 14)) return 0;
+    uint64_t *r = (uint64_t *)malloc((N + 3) * sizeof(uint64_t));
+    if (!r) return 0;
+    r[0] = 0;
+    for (uint64_t x = 1; x <= N + 2; x++) r[x] = orc_rad_td(x);
+    const size_t cnt = orc_pairs_brute_rad(r, N, kinds, out, cap);
+    free(r);
     return cnt;
 }
 

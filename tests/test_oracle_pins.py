@@ -79,7 +79,32 @@ def pin_crt(o):
     return bad
 
 
-ALL_PINS = [pin_tables, pin_sieve_edges, pin_brute, pin_sort, pin_crt]
+def pin_pairs_on_planted_radicals(o):
+    """The definitions of Sec. 1 on a fabricated radical array (no real radicals give a
+    three-term pair): distinct values everywhere, then collisions planted for a
+    three-term pair (5, 20) -- which makes (6, 21) a first-kind pair too, since
+    r[6] = r[21] and r[7] = r[22] -- a first-kind pair without the third term
+    (10, 25), and a second-kind pair (30, 35)."""
+    import numpy as np
+
+    N = 40
+    r = np.arange(1000, 1000 + N + 2, dtype=np.uint64)
+    r[0] = 0
+    r[20], r[21], r[22] = r[5], r[6], r[7]      # rad(m + i) = rad(n + i), i = 0, 1, 2
+    r[25], r[26] = r[10], r[11]                 # first kind only: r[12] != r[27]
+    r[36], r[35] = r[30], r[31]                 # second kind: r[30] = r[36], r[31] = r[35]
+    first = [(5, 20, 1), (6, 21, 1), (10, 25, 1)]
+    key = lambda p: (p[1], p[0], p[2])
+    bad = []
+    for kinds, exp in ((1, first), (2, [(30, 35, 2)]), (4, [(5, 20, 4)]),
+                       (7, sorted(first + [(30, 35, 2), (5, 20, 4)], key=key))):
+        got = o.pairs_brute_rad(r, N, kinds)
+        if got != exp:
+            bad.append(f"planted radicals, kinds {kinds}: {got} != {exp}")
+    return bad
+
+
+ALL_PINS = [pin_tables, pin_sieve_edges, pin_brute, pin_pairs_on_planted_radicals, pin_sort, pin_crt]
 
 
 # ---------------------------------------------------------------------------
@@ -190,7 +215,8 @@ def test_nprimes(orc):
 MUTANTS = {1: "rad_td drops the last prime cofactor", 2: "Alg. 1 misses the multiple at start",
            3: "Alg. 1 starts at exponent 1", 4: "Alg. 2 kind rule inverted",
            5: "CRT second kind m = j*ab - n", 6: "first-kind inequality used for the second kind",
-           7: "Alg. 1 sieves primes p < sqrt(S) only", 8: "brute force transposes an operand"}
+           7: "Alg. 1 sieves primes p < sqrt(S) only", 8: "brute force transposes an operand",
+           9: "three-term rule compares m + 2 with n + 1"}
 
 
 @pytest.mark.parametrize("k", sorted(MUTANTS), ids=lambda k: f"mutant{k}")
