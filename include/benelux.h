@@ -218,6 +218,16 @@ uint32_t bnx_log_weight(uint64_t p, uint32_t frac_log2);
  * number of primes.  Blocking.  Errors: BNX_E_ARG, BNX_E_TRUNCATED, BNX_E_CUDA. */
 int bnx_log_weights(bnx_ctx *ctx, uint32_t tile_kind, uint32_t *out, size_t cap, size_t *n_out);
 
+/* rad(x[i]) == rad(y[i]) for n pairs, on the current device, by the gcd strips
+ * the verification kernel applies to a candidate (the same device function:
+ * strip from x every common factor with y until 1 remains, and the same the
+ * other way).  This is the test behind Erdos's three-term question (Sec. 1):
+ * a first-kind pair (m, n) is also a three-term pair when rad(m+2) = rad(n+2).
+ * x, y are HOST arrays of n values >= 1; out is a HOST array of n bytes
+ * (1: equal radicals, 0: not); n <= 2^24.  Device scratch is allocated and
+ * freed inside the call; blocking.  Errors: BNX_E_ARG, BNX_E_NOMEM, BNX_E_CUDA. */
+int bnx_same_rad(const uint64_t *x, const uint64_t *y, size_t n, uint8_t *out);
+
 /* ------------------------------------------------------------------------ */
 /* Searches                                                                    */
 /* ------------------------------------------------------------------------ */

@@ -92,6 +92,7 @@ def lib(auto_build: bool = True):
             "bnx_rad_segment": ([vp, u64, u64, vp, vp, vp], i32),
             "bnx_rad_segment_noalloc": ([u64, u64, vp, vp, vp], i32),
             "bnx_log_weight": ([u64, u32], u32),
+            "bnx_same_rad": ([P(u64), P(u64), sz, P(ctypes.c_uint8)], i32),
             "bnx_log_weights": ([vp, u32, P(u32), sz, P(sz)], i32),
             "bnx_search": ([vp, u64, u64, u32, P(bnx_pair), sz, P(sz)], i32),
             "bnx_search_segment": ([vp, u64, u32, u32, P(bnx_pair), sz, P(sz)], i32),
@@ -196,6 +197,19 @@ def bnx_rad_segment_noalloc(lo: int, length: int, rad_out_ptr: int, sq_out_ptr: 
 def bnx_log_weight(p: int, frac_log2: int) -> int:
     """Smallest L with 2^L > p^(2^frac_log2), in integers (host only)."""
     return int(lib().bnx_log_weight(p, frac_log2))
+
+
+def bnx_same_rad(x, y):
+    """rad(x[i]) == rad(y[i]) per pair, on the device (the verification kernel's test)."""
+    import numpy as np
+
+    xa = np.ascontiguousarray(x, dtype=np.uint64)
+    ya = np.ascontiguousarray(y, dtype=np.uint64)
+    assert xa.shape == ya.shape
+    out = np.zeros(xa.size, dtype=np.uint8)
+    _check(lib().bnx_same_rad(xa.ctypes.data_as(ctypes.POINTER(u64)), ya.ctypes.data_as(ctypes.POINTER(u64)),
+                              xa.size, out.ctypes.data_as(ctypes.POINTER(ctypes.c_uint8))))
+    return out.astype(bool)
 
 
 def bnx_log_weights(ctx, tile_kind: int = 3):

@@ -243,6 +243,8 @@ uint32_t sched_length(uint32_t tile_log2, const uint32_t *q, uint32_t nspp);
 
 // verify.cu
 void launch_verify(const Plan &P, int grid, cudaStream_t s);
+// out[i] = (rad(x[i]) == rad(y[i])), by k_verify's gcd strips
+void launch_same_rad(const uint64_t *x, const uint64_t *y, uint64_t n, uint8_t *out, cudaStream_t s);
 void launch_sort(const Plan &P, int grid, cudaStream_t s);
 void launch_offsets(const Plan &P, int grid, cudaStream_t s);
 void launch_hash_insert(const Plan &P, int grid, cudaStream_t s);

@@ -821,6 +821,32 @@ extern "C" {
 
 uint32_t bnx_log_weight(uint64_t p, uint32_t frac_log2) { return log_weight(p, frac_log2); }
 
+int bnx_same_rad(const uint64_t *x, const uint64_t *y, size_t n, uint8_t *out) {
+    if (n == 0) return BNX_OK;
+    if (!x || !y || !out) return fail(BNX_E_ARG, "NULL argument");
+    if (n > ((size_t)1 << 24)) return fail(BNX_E_ARG, "at most 2^24 pairs per call");
+    for (size_t i = 0; i < n; i++)
+        if (x[i] == 0 || y[i] == 0) return fail(BNX_E_ARG, "values must be >= 1 (pair %zu)", i);
+    DevBuf b;
+    int rc = grow(b, n * (2 * sizeof(uint64_t) + 1));
+    if (rc) return rc;
+    uint64_t *dx = (uint64_t *)b.p, *dy = dx + n;
+    uint8_t *dout = (uint8_t *)(dy + n);
+    cudaError_t e = cudaMemcpy(dx, x, n * sizeof(uint64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) e = cudaMemcpy(dy, y, n * sizeof(uint64_t), cudaMemcpyHostToDevice);
+    if (e == cudaSuccess) {
+        launch_same_rad(dx, dy, n, dout, nullptr);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(out, dout, n, cudaMemcpyDeviceToHost);
+    release(b);
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(BNX_E_CUDA, "same_rad: %s", cudaGetErrorString(e));
+    }
+    return BNX_OK;
+}
+
 int bnx_log_weights(bnx_ctx *c, uint32_t tile_kind, uint32_t *out, size_t cap, size_t *n_out) {
     if (!c || !n_out) return fail(BNX_E_ARG, "NULL argument");
     if (tile_kind != kTileLog32 && tile_kind != kTileLog16 && tile_kind != kTileLog8)

@@ -201,8 +201,18 @@ __global__ void k_hash_pairs(Plan P, uint32_t kinds) {
     }
 }
 
+// out[i] = rad(x[i]) == rad(y[i]) by the gcd strips k_verify uses (its three-term test)
+__global__ void k_same_rad(const uint64_t *x, const uint64_t *y, uint64_t n, uint8_t *out) {
+    for (uint64_t i = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; i < n; i += (uint64_t)gridDim.x * blockDim.x)
+        out[i] = same_rad(x[i], y[i]) ? 1 : 0;
+}
+
 }  // namespace
 
+void launch_same_rad(const uint64_t *x, const uint64_t *y, uint64_t n, uint8_t *out, cudaStream_t s) {
+    const uint64_t blocks = (n + 255) / 256;
+    k_same_rad<<<(unsigned)(blocks < 4096 ? (blocks ? blocks : 1) : 4096), 256, 0, s>>>(x, y, n, out);
+}
 void launch_verify(const Plan &P, int grid, cudaStream_t s) { k_verify<<<grid, 256, 0, s>>>(P); }
 void launch_sort(const Plan &P, int grid, cudaStream_t s) { k_sort<<<grid, 256, 0, s>>>(P); }
 void launch_offsets(const Plan &P, int grid, cudaStream_t s) { k_offsets<<<grid, 256, 0, s>>>(P); }

@@ -107,3 +107,19 @@ def test_ncu_record_follows_the_code_not_the_comments(tmp_path):
     assert bench.code_sha256(str(src)) == h
     src.write_text("int f(int x) {\n    return x + 2;\n}\n")
     assert bench.code_sha256(str(src)) != h
+    assert bench.sieve_record(3) is not None  # the committed capture matches the current kernel
+
+
+def test_same_rad_rejects_bad_arguments_before_the_device(lib):
+    """bnx_same_rad checks its arguments on the host first (no device is touched)."""
+    from paper_2506_01099_gb300 import benelux as B
+
+    P = ctypes.POINTER(ctypes.c_uint64)
+    x = (ctypes.c_uint64 * 2)(6, 0)
+    y = (ctypes.c_uint64 * 2)(12, 5)
+    out = (ctypes.c_uint8 * 2)()
+    assert lib.bnx_same_rad(x, y, 0, out) == B.BNX_OK  # nothing to do
+    assert lib.bnx_same_rad(x, y, 2, out) == B.BNX_E_ARG  # a zero value
+    assert lib.bnx_same_rad(None, y, 1, out) == B.BNX_E_ARG
+    assert lib.bnx_same_rad(x, y, 1, None) == B.BNX_E_ARG
+    assert lib.bnx_same_rad(ctypes.cast(x, P), ctypes.cast(y, P), (1 << 24) + 1, out) == B.BNX_E_ARG

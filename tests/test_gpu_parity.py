@@ -558,3 +558,55 @@ def test_autotune_picks_a_sound_tuning(B, orc):
         pairs, offs = c.batch(ivs)
         for i, iv in enumerate(ivs):
             assert [(m, n, kd) for (_, m, n, kd) in pairs[offs[i]:offs[i + 1]]] == theorem1_pairs(iv.lo, iv.hi, iv.kinds)
+
+
+def test_same_rad_on_constructed_pairs(B, orc):
+    """The gcd strips behind the three-term test (rad(m+2) = rad(n+2), Sec. 1) on pairs
+    built from chosen factorisations -- equal prime supports with different exponents,
+    one prime swapped, edge values -- and on random pairs against the oracle's radicals."""
+    import math
+
+    rng = np.random.default_rng(7)
+    small = [2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37, 41, 43, 47, 53, 59, 61, 67, 71, 73, 79, 83, 89, 97]
+    big = [1000003, 2147483647, 4294967291]
+    xs, ys, want = [], [], []
+
+    def add(x, y, w):
+        xs.append(x)
+        ys.append(y)
+        want.append(w)
+
+    for _ in range(3000):
+        k = int(rng.integers(1, 5))
+        supp = [int(p) for p in rng.choice(small, k, replace=False)]
+        if rng.random() < 0.3:
+            supp[0] = int(rng.choice(big))
+        x = y = 1
+        for p in supp:
+            x *= p ** int(rng.integers(1, 4))
+            y *= p ** int(rng.integers(1, 4))
+        if x >= 1 << 63 or y >= 1 << 63:
+            continue
+        if rng.random() < 0.5:
+            add(x, y, True)
+        else:  # swap one prime of y's support for one outside it
+            p = supp[int(rng.integers(0, k))]
+            q = next(int(v) for v in rng.permutation(small) if int(v) not in supp)
+            y2 = y
+            while y2 % p == 0:
+                y2 //= p
+            y2 *= q
+            if y2 < 1 << 63:
+                add(x, y2, False)
+    for x, y, w in ((1, 1, True), (1, 2, False), (2, 1, False), (2**62, 2, True), (3**39, 3, True), (3 * 2**40, 6, True),
+                    (6, 10, False), (2147483647 * 3, 2147483647, False), (2147483647**2, 2147483647, True),
+                    (1000003 * 65537, 1000003**2 * 65537, True), (77, 1217, False)):
+        add(x, y, w)
+    for x, y in rng.integers(1, 1 << 40, size=(500, 2)):
+        add(int(x), int(y), orc.rad_td(int(x)) == orc.rad_td(int(y)))
+    for m, n, _ in theorem1_pairs(1, 1 << 40, 1):  # the families fail the three-term question (Sec. 1)
+        add(m + 2, n + 2, orc.rad_td(m + 2) == orc.rad_td(n + 2))
+    got = B.bnx_same_rad(xs, ys)
+    bad = [(xs[i], ys[i], want[i]) for i in range(len(xs)) if bool(got[i]) != want[i]]
+    assert not bad, bad[:5]
+    assert sum(want) > 1000 and len(want) - sum(want) > 1000
