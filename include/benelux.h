@@ -340,7 +340,8 @@ int bnx_server_get_stats(bnx_ctx *ctx, bnx_server_stats *out);
 
 /* Device workspace, in bytes, that one batched run over these k intervals
  * needs (bnx_batch sizes its workspace to at least this; the serving loop's
- * admission uses the same figure).  `iv` is a HOST array.  Errors: BNX_E_ARG. */
+ * admission uses the same figure).  `iv` is a HOST array.  Not while the
+ * serving loop runs.  Errors: BNX_E_ARG, BNX_E_STATE. */
 int bnx_workspace_bytes(bnx_ctx *ctx, const bnx_interval *iv, size_t k, uint64_t *bytes);
 
 /* Queue a request; *ticket identifies it.  Never blocks on the device. */

@@ -210,6 +210,7 @@ int bnx_server_start(bnx_ctx *c, const bnx_server_cfg *cfg) {
         S->budget = (uint64_t)(0.9 * (double)fr);
     }
     S->st.budget_bytes = S->budget;
+    publish_stats(c, *S);  // this loop's counters from the start
     S->buf.resize(4096);
     c->server = S;
     c->serving.store(true);
@@ -290,6 +291,7 @@ int bnx_server_get_stats(bnx_ctx *c, bnx_server_stats *out) {
 int bnx_workspace_bytes(bnx_ctx *c, const bnx_interval *iv, size_t k, uint64_t *bytes) {
     if (!c || !bytes || (!iv && k)) return fail(BNX_E_ARG, "NULL argument");
     if (k > (1u << 24)) return fail(BNX_E_ARG, "at most 2^24 intervals per batch");
+    if (c->server_running()) return fail(BNX_E_STATE, "the serving loop owns the context");
     std::vector<IvDev> d(k);
     for (size_t i = 0; i < k; i++) {
         int rc = validate_interval(c, iv[i].lo, iv[i].hi, iv[i].kinds);
