@@ -75,10 +75,13 @@ struct bnx_ctx {
     // hash-mode parameters of the current call
     uint64_t hash_S = 0, hash_mask = 0;
 
-    // graph of the search pipeline
-    cudaGraphExec_t gexec = nullptr;
-    bool graph_valid = false;
+    // graphs of the search pipeline, one per queue-segment length (2^tile_log2 .. 2^(tile_log2+6))
+    static constexpr int kGraphSlots = 7;
+    cudaGraphExec_t gexec[kGraphSlots] = {};
+    bool graph_ok[kGraphSlots] = {};
     bool capturing = false;
+    // queue-segment length of the current run (log2); 0: the tuned one
+    uint32_t seg_log2_run = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr, ev_s0 = nullptr, ev_s1 = nullptr;
 
     uint32_t lb_spin_limit = 0;  // nonzero: the next bnx_search_sorted runs the look-back test hook
@@ -91,10 +94,14 @@ struct bnx_ctx {
     bnx_server_stats srv_stats{};  // of the current or last serving loop
 
     uint32_t n_sched() const { return bnx::sched_length(tune.tile_log2, h_spp_q.data(), n_spp); }
-    uint32_t seg_log2() const {
+    uint32_t seg_log2_tuned() const {
         uint32_t l = 0;
         while ((1u << l) < tune.seg_tiles) l++;
         return tune.tile_log2 + l;
+    }
+    uint32_t seg_log2() const { return seg_log2_run ? seg_log2_run : seg_log2_tuned(); }
+    void invalidate_graphs() {
+        for (bool &v : graph_ok) v = false;
     }
     uint32_t chunk_log2() const { return seg_log2() + bnx::kChunkSegsLog2; }
     bool server_running() const { return serving.load(); }

@@ -176,7 +176,7 @@ struct Plan {
     uint32_t sqrt_q;   // floor(sqrt(Q)): primes above it reach the tile only through buckets
     const LargePP *lpp;  // sorted by q
     uint32_t n_lpp;
-    uint32_t n_lpp_dense;  // entries with q <= 2^(chunk_log2 - 8): walked by a whole warp
+    uint32_t n_lpp_dense;  // entries with q <= min(2^(chunk_log2 - 5), 2^20): walked by a whole warp
     uint32_t tile_log2, seg_log2;  // tile 2^tile_log2 integers, queue segment 2^seg_log2
     uint32_t chunk_log2;           // bucket-fill chunk: 2^chunk_log2 sieved values
     uint32_t *bcnt;                // [seg capacity]

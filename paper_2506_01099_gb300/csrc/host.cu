@@ -332,7 +332,7 @@ int ensure_ws(bnx_ctx *c, const PlanTotals &t, size_t k, uint64_t budget) {
         changed = true;
         if ((rc = grow(*b[i], tight ? v[i] : v[i] + v[i] / 4))) return rc;
     }
-    if (changed) c->graph_valid = false;
+    if (changed) c->invalidate_graphs();
     return ensure_staging(c, k);
 }
 
@@ -369,7 +369,9 @@ Plan make_plan(const bnx_ctx *c) {
     P.seg_log2 = c->seg_log2();
     P.chunk_log2 = c->chunk_log2();
     {
-        const uint64_t qd = 1ull << (P.chunk_log2 - 8);
+        // walked by a whole warp: prime powers with at least 32 multiples per chunk (one
+        // full warp round), up to 2^20 (above that one thread per q measured faster)
+        const uint64_t qd = std::min<uint64_t>(1ull << (P.chunk_log2 - 5), 1ull << 20);
         P.n_lpp_dense = (uint32_t)(std::upper_bound(c->lq.begin(), c->lq.end(), qd) - c->lq.begin());
     }
     P.bcnt = (uint32_t *)c->bcnt.p;
@@ -493,9 +495,11 @@ int run_search(bnx_ctx *c, size_t k, bool use_graph) {
     CUDA_TRY(cudaMemcpyAsync(c->n_iv.p, &c->h_nk, sizeof(uint32_t), cudaMemcpyHostToDevice, s));
     CUDA_TRY(cudaEventRecord(c->ev0, s));
     if (use_graph) {
-        if (!c->graph_valid) {
-            if (c->gexec) cudaGraphExecDestroy(c->gexec);
-            c->gexec = nullptr;
+        const uint32_t slot = c->seg_log2() - c->tune.tile_log2;  // < kGraphSlots: segments hold 1 .. 64 tiles
+        cudaGraphExec_t &gexec = c->gexec[slot];
+        if (!c->graph_ok[slot]) {
+            if (gexec) cudaGraphExecDestroy(gexec);
+            gexec = nullptr;
             cudaGraph_t g;
             int sg, st;
             size_t ss;
@@ -511,12 +515,12 @@ int run_search(bnx_ctx *c, size_t k, bool use_graph) {
                 return rc;
             }
             if (e != cudaSuccess) return fail(BNX_E_CUDA, "graph capture failed: %s", cudaGetErrorString(e));
-            e = cudaGraphInstantiate(&c->gexec, g, 0);
+            e = cudaGraphInstantiate(&gexec, g, 0);
             cudaGraphDestroy(g);
             if (e != cudaSuccess) return fail(BNX_E_CUDA, "graph instantiate failed: %s", cudaGetErrorString(e));
-            c->graph_valid = true;
+            c->graph_ok[slot] = true;
         }
-        CUDA_TRY(cudaGraphLaunch(c->gexec, s));
+        CUDA_TRY(cudaGraphLaunch(gexec, s));
     } else {
         int rc = record_pipeline(c, kModeSearch, s, true);
         if (rc) return rc;
@@ -688,7 +692,8 @@ void bnx_destroy(bnx_ctx *c) {
     bnx_server_stop(c);
     cudaSetDevice(c->device);
     if (c->stream) cudaStreamSynchronize(c->stream);
-    if (c->gexec) cudaGraphExecDestroy(c->gexec);
+    for (cudaGraphExec_t g : c->gexec)
+        if (g) cudaGraphExecDestroy(g);
     for (DevBuf *b : c->all_bufs()) release(*b);
     if (c->h_ctr) cudaFreeHost(c->h_ctr);
     if (c->h_ivs) cudaFreeHost(c->h_ivs);
@@ -722,7 +727,7 @@ int bnx_set_tune(bnx_ctx *c, const bnx_tune *t) {
         build_pp_tables(c);
         return rc;
     }
-    c->graph_valid = false;
+    c->invalidate_graphs();
     return BNX_OK;
 }
 
@@ -876,6 +881,23 @@ int bnx_log_weights(bnx_ctx *c, uint32_t tile_kind, uint32_t *out, size_t cap, s
 
 }  // extern "C"
 
+// Queue-segment length (log2) for a run over one interval of len integers: the tuned
+// length, or shorter (down to one tile) when the interval would otherwise give fewer
+// than about two segments per CTA of the persistent grid -- a short search then still
+// spreads over many CTAs instead of running on a few.
+static uint32_t single_seg_log2(bnx_ctx *c, uint64_t len) {
+    const uint32_t tuned = c->seg_log2_tuned();
+    int grid = 0, threads = 0;
+    size_t smem = 0;
+    if (sieve_config(c, kModeSearch, &grid, &threads, &smem) != BNX_OK || grid <= 0) {
+        g_last_error.clear();
+        return tuned;  // the run itself reports the problem
+    }
+    uint32_t s = c->tune.tile_log2;
+    while (s < tuned && ((uint64_t)4 << s) * (uint64_t)grid <= len) s++;
+    return s;
+}
+
 // One n-range through the staged pipeline (bnx_search and bnx_search_segment).
 static int search_one(bnx_ctx *c, uint64_t lo, uint64_t hi, uint32_t kinds, bnx_pair *out, size_t cap,
                       size_t *n_out) {
@@ -884,6 +906,11 @@ static int search_one(bnx_ctx *c, uint64_t lo, uint64_t hi, uint32_t kinds, bnx_
     if (c->server_running()) return fail(BNX_E_STATE, "the serving loop owns the context");
     std::lock_guard<std::mutex> g(c->mu);
     cudaSetDevice(c->device);
+    struct SegGuard {  // the run's segment length, back to the tuned one on every return
+        bnx_ctx *c;
+        ~SegGuard() { c->seg_log2_run = 0; }
+    } seg_guard{c};
+    c->seg_log2_run = single_seg_log2(c, hi - lo);
     PlanTotals t;
     IvDev iv;
     memset(&iv, 0, sizeof iv);

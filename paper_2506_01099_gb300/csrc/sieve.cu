@@ -105,7 +105,7 @@ __global__ void k_plan(IvDev *ivs, const uint32_t *n_iv_dev, uint32_t seg_log2, 
 // chunk's own segments live in shared memory; only a halo that belongs to the
 // previous chunk's last segment goes through a global counter (those entries
 // are written from the end of that segment's bucket, so the two writers never
-// meet).  Prime powers with many multiples per chunk (q <= 2^(chunk_log2-8))
+// meet).  Prime powers with many multiples per chunk (at least 32, and q <= 2^20)
 // are walked by a whole warp, the rest one thread each; the table is sorted by
 // q, so a thread stops at the first q above the chunk.
 constexpr uint32_t kChunkSegs = 1u << kChunkSegsLog2;
