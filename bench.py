@@ -395,6 +395,10 @@ def run_ours(args):
         extras["materialised_rad"] = materialised_rad(ctx, torch, stream)
         extras["serving"] = serve_stream(B, ctx, args, throughput=value / ws)
         extras["serving_saturated"] = serve_stream(B, ctx, args, throughput=value / ws, saturate=True)
+        # the same Poisson stream with 4x shorter slices: shorter iterations, lower latency, more
+        # per-iteration overhead
+        extras["serving_short_slices"] = serve_stream(B, ctx, args, throughput=value / ws,
+                                                      slice_len=max(1 << 20, args.serve_slice // 4))
 
     if rank == 0:
         pk, pk_src = peaks()
@@ -486,7 +490,7 @@ def full_range_2p32(ctx):
 
 
 def materialised_rad(ctx, torch, stream):
-    """The HBM-writing counterpoint to the fused search: bnx_rad_segment writes
+    """The HBM-writing counterpoint to the fused search: bnx_rad_segment (k_rad) writes
     the radical and the square part of each of the 2^31 integers
     [2^40, 2^40 + 2^31) to HBM (16 B per integer), CUDA-event timed."""
     lo, n = 1 << 40, 1 << 31
@@ -506,10 +510,10 @@ def materialised_rad(ctx, torch, stream):
     gbs = 16 * n / (ms / 1e3) / 1e9
     return {"range": [lo, lo + n], "integers_per_s": n / (ms / 1e3), "ms": ms, "written_GBps": gbs,
             "hbm_frac": gbs / hbm, "first_value_ok": check,
-            "note": "exact u64 tile sieve writing rad and the square part; the fused search writes neither"}
+            "note": "k_rad (u32 square-part tile) writing rad and the square part; the fused search writes neither"}
 
 
-def serve_stream(B, ctx, args, throughput: float, saturate: bool = False):
+def serve_stream(B, ctx, args, throughput: float, saturate: bool = False, slice_len: int | None = None):
     """Seeded Poisson stream at 0.7x the batched throughput (or, saturated, every
     request at t = 0); p50/p99 latency and integers/s."""
     n = args.serve_requests
@@ -518,7 +522,8 @@ def serve_stream(B, ctx, args, throughput: float, saturate: bool = False):
     reqs = W.serving_requests(n, rate_per_s=rate)
     if saturate:
         reqs = [W.Request(0.0, r.interval) for r in reqs]
-    B.bnx_server_start(ctx.h, max_active=args.serve_slots, slice_len=args.serve_slice)
+    slice_len = slice_len or args.serve_slice
+    B.bnx_server_start(ctx.h, max_active=args.serve_slots, slice_len=slice_len)
     lat = {}
     tickets = {}
     t0 = time.perf_counter()
@@ -545,7 +550,7 @@ def serve_stream(B, ctx, args, throughput: float, saturate: bool = False):
     q = lambda p: ls[min(len(ls) - 1, int(math.ceil(p * len(ls))) - 1)] if ls else None
     return {"requests": n, "completed": len(ls), "rate_per_s": None if saturate else rate,
             "p50_s": q(0.50), "p99_s": q(0.99),
-            "integers_per_s": integers / span, "span_s": span, "slots": args.serve_slots, "slice": args.serve_slice,
+            "integers_per_s": integers / span, "span_s": span, "slots": args.serve_slots, "slice": slice_len,
             "note": ("all requests submitted at t = 0" if saturate else
                      "seeded Poisson arrivals at 0.7x batched throughput / E[len]") +
                     "; len log-uniform [2^20, 2^34], lo uniform [1, 1.4e12], kinds 1|2|3"}
@@ -587,6 +592,26 @@ def profile_sorted(lg: int):
     return 0
 
 
+def profile_rad(lg: int):
+    """One warm-up and one bnx_rad_segment of 2^lg values at 2^40, rad and square part
+    (the k_rad case for ncu)."""
+    import torch
+
+    from paper_2506_01099_gb300 import benelux as B
+
+    ctx = B.Context(0, max_hi=MAX_HI)
+    n = 1 << lg
+    rad = torch.empty(n, dtype=torch.int64, device="cuda")
+    sq = torch.empty(n, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.current_stream().cuda_stream
+    for _ in range(2):
+        ctx.rad_segment(1 << 40, n, rad.data_ptr(), sq.data_ptr(), stream)
+    torch.cuda.synchronize()
+    print(json.dumps({"profile_rad": [1 << 40, (1 << 40) + n], "rad0": int(rad[0].item()), "sq0": int(sq[0].item())}))
+    ctx.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -609,9 +634,13 @@ def main():
                     help="window length of --profile-case as a power of two (default 28)")
     ap.add_argument("--profile-sorted", type=int, default=0, metavar="LG",
                     help="one Algorithm 2 search of all n < 2^LG (small case for ncu), then exit")
+    ap.add_argument("--profile-rad", type=int, default=0, metavar="LG",
+                    help="radicals and square parts of 2^LG values at 2^40 (small case for ncu), then exit")
     args = ap.parse_args()
     if args.profile_sorted:
         return profile_sorted(args.profile_sorted)
+    if args.profile_rad:
+        return profile_rad(args.profile_rad)
     if args.profile_case:
         return profile_case(args.tune, args.profile_len_log2)
     if args.impl == "reference":

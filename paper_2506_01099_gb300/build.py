@@ -18,7 +18,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libbenelux.so")
-SOURCES = ["tables.cu", "sieve.cu", "sieve_log.cu", "verify.cu", "host.cu", "server.cu", "noalloc.cu", "alg3.cu", "alg2.cu"]
+SOURCES = ["tables.cu", "sieve.cu", "sieve_log.cu", "rad.cu", "verify.cu", "host.cu", "server.cu", "noalloc.cu",
+           "alg3.cu", "alg2.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

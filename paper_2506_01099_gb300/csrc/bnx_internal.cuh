@@ -229,6 +229,10 @@ void launch_plan(const Plan &P, uint32_t *n_iv_dev, IvDev *ivs, uint64_t max_iv,
 void launch_bucket(const Plan &P, bool fill, int grid, cudaStream_t s);
 void launch_sieve(const Plan &P, int mode, int grid, int threads, size_t smem, cudaStream_t s);
 int sieve_occupancy(int mode, int threads, size_t smem, int *ctas_per_sm);
+// rad.cu: exact radicals (rad mode)
+void launch_rad(const Plan &P, int grid, int threads, size_t smem, cudaStream_t s);
+int rad_occupancy(int threads, size_t smem, int *ctas_per_sm);
+size_t rad_smem_bytes(uint32_t tile_log2, uint32_t nspp, uint32_t nsched);
 // sieve_log.cu: log-domain tile for the search and hash modes
 // vb: bytes per tile value (4, 2 or 1)
 void launch_sieve_log(const Plan &P, int mode, int vb, int grid, int threads, size_t smem, cudaStream_t s);

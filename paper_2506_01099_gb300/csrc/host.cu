@@ -410,8 +410,9 @@ Plan make_plan(const bnx_ctx *c) {
 // any stream capture and cached until the tuning changes).
 static bool use_log_tile(const bnx_ctx *c, int mode) { return mode != kModeRad && c->tune.tile_kind != kTileExact; }
 
-// The exact u64 tile fits shared memory up to 2^14 values; a longer tuned tile
-// is processed by it as several tiles of the same queue segment.
+// The exact u64 tile (searches) and the u32 radical tile fit shared memory up to
+// 2^14 values; a longer tuned tile is processed as several tiles of the same
+// queue segment.
 static uint32_t tile_log2_for(const bnx_ctx *c, int mode) {
     return use_log_tile(c, mode) ? c->tune.tile_log2 : std::min<uint32_t>(c->tune.tile_log2, 14u);
 }
@@ -426,15 +427,18 @@ int sieve_config(bnx_ctx *c, int mode, int *grid, int *threads, size_t *smem) {
     SieveCfg &sc = c->sieve_cfg[mode * 4 + (lg ? (vb == 4 ? 1 : vb == 2 ? 2 : 3) : 0)];
     const uint32_t tlog = tile_log2_for(c, mode);
     const uint32_t nsched = sched_length(tlog, c->h_spp_q.data(), c->n_spp);
-    const size_t want_smem = lg ? sieve_log_smem_bytes(tlog, c->n_spp, nsched, vb)
-                                : sieve_smem_bytes(tlog, c->n_spp, nsched);
+    const size_t want_smem = lg                ? sieve_log_smem_bytes(tlog, c->n_spp, nsched, vb)
+                             : mode == kModeRad ? rad_smem_bytes(tlog, c->n_spp, nsched)
+                                                : sieve_smem_bytes(tlog, c->n_spp, nsched);
     if (!sc.valid || sc.tile_log2 != tlog || sc.threads != c->tune.threads ||
         sc.ctas != c->tune.ctas_per_sm || sc.smem != want_smem) {
         if (c->capturing) return fail(BNX_E_STATE, "sieve launch shape unknown during capture");
         const int thr = (int)c->tune.threads;
         const size_t smem_b = want_smem;
         int occ = 0;
-        int e = lg ? sieve_log_occupancy(mode, thr, vb, smem_b, &occ) : sieve_occupancy(mode, thr, smem_b, &occ);
+        int e = lg                ? sieve_log_occupancy(mode, thr, vb, smem_b, &occ)
+                : mode == kModeRad ? rad_occupancy(thr, smem_b, &occ)
+                                   : sieve_occupancy(mode, thr, smem_b, &occ);
         if (e != 0) return fail(BNX_E_CUDA, "sieve occupancy query failed: %s", cudaGetErrorString((cudaError_t)e));
         if (occ < 1) return fail(BNX_E_ARG, "sieve kernel does not fit an SM with this tuning");
         const int per = c->tune.ctas_per_sm ? std::min<int>((int)c->tune.ctas_per_sm, occ) : occ;
@@ -472,6 +476,7 @@ int record_pipeline(bnx_ctx *c, int mode, cudaStream_t s, bool timing) {
     launch_bucket(P, true, bgrid, s);
     if (timing) CUDA_TRY(cudaEventRecordWithFlags(c->ev_s0, s, c->capturing ? cudaEventRecordExternal : 0));
     if (use_log_tile(c, mode)) launch_sieve_log(P, mode, log_vb(c), sgrid, sthreads, ssmem, s);
+    else if (mode == kModeRad) launch_rad(P, sgrid, sthreads, ssmem, s);
     else launch_sieve(P, mode, sgrid, sthreads, ssmem, s);
     if (timing) CUDA_TRY(cudaEventRecordWithFlags(c->ev_s1, s, c->capturing ? cudaEventRecordExternal : 0));
     if (use_log_tile(c, mode)) launch_cand(P, mode, c->n_sm * 2, s);

@@ -291,7 +291,7 @@ struct MinBlocks {
 template <int MODE, int NT>
 __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_sieve(Plan P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr bool MARK = MODE != kModeRad;
+    constexpr bool MARK = true;  // search and hash modes (the radicals have their own kernel, rad.cu)
     const uint32_t tile_log2 = P.tile_log2;
     const uint32_t LT = 1u << tile_log2;
     const uint32_t nspp = P.n_spp;
@@ -441,70 +441,57 @@ __global__ void __launch_bounds__(NT, MinBlocks<NT>::value) k_sieve(Plan P) {
                 soff[j] = off >= lm ? off - lm : off + sq[j] - lm;
             }
 
-            if (MODE == kModeRad) {
-                for (uint32_t i = tid; i < tl; i += NT) {
-                    const uint64_t x = t_lo + i;
-                    const uint64_t gi = x - P.rad_lo;
-                    if (gi < P.rad_len) {
-                        const uint32_t tz = ctz64(x);
-                        const uint64_t s = tile[i] << (tz ? tz - 1 : 0);
-                        P.rad_out[gi] = x / s;
-                        if (P.sq_out) P.sq_out[gi] = s;
+            // sparse epilogue: only the marked n and the n next to a multiple of 2^9
+            constexpr uint32_t M2 = 1u << kHighTwoLog2;
+            for (uint32_t w0 = warp * 32; w0 < nwords; w0 += nwarps * 32) {
+                const uint32_t w = w0 + lane;
+                uint32_t bits = 0;
+                if (w < nwords) {
+                    bits = bitmap[w];
+                    if (tau != 0) {
+                        const uint32_t r = (uint32_t)((t_lo + 32ull * w) & (M2 - 1));
+                        const uint32_t d0 = (M2 - r) & (M2 - 1);  // bit of the n with 2^9 | n
+                        const uint32_t d1 = (d0 + M2 - 1) & (M2 - 1);  // bit of the n with 2^9 | n+1
+                        if (d0 < 32) bits |= 1u << d0;
+                        if (d1 < 32) bits |= 1u << d1;
                     }
+                    const uint32_t lim = tl - 32 * w;  // >= 1
+                    if (lim < 32) bits &= (1u << lim) - 1;
                 }
-            } else {
-                // sparse epilogue: only the marked n and the n next to a multiple of 2^9
-                constexpr uint32_t M2 = 1u << kHighTwoLog2;
-                for (uint32_t w0 = warp * 32; w0 < nwords; w0 += nwarps * 32) {
-                    const uint32_t w = w0 + lane;
-                    uint32_t bits = 0;
-                    if (w < nwords) {
-                        bits = bitmap[w];
-                        if (tau != 0) {
-                            const uint32_t r = (uint32_t)((t_lo + 32ull * w) & (M2 - 1));
-                            const uint32_t d0 = (M2 - r) & (M2 - 1);  // bit of the n with 2^9 | n
-                            const uint32_t d1 = (d0 + M2 - 1) & (M2 - 1);  // bit of the n with 2^9 | n+1
-                            if (d0 < 32) bits |= 1u << d0;
-                            if (d1 < 32) bits |= 1u << d1;
-                        }
-                        const uint32_t lim = tl - 32 * w;  // >= 1
-                        if (lim < 32) bits &= (1u << lim) - 1;
+                while (__any_sync(0xffffffffu, bits != 0)) {
+                    uint32_t kk = 0;
+                    uint64_t n = 0, a = 0, b = 0;
+                    if (bits) {
+                        const uint32_t i = 32 * w + (uint32_t)(__ffs(bits) - 1);
+                        bits &= bits - 1;
+                        n = t_lo + i;
+                        const uint64_t s0 = tile[i], s1 = tile[i + 1];
+                        // bit-length bound first: s(n)s(n+1) < 2^lb, power of 2 included
+                        const int lb = (int)(bitlen64(s0) + bitlen64(s1) + ctz64(n + (n & 1))) - 1;
+                        if (lb > thr_lb) kk = exact_kinds(n, s0, s1, kinds, MODE, P.hash_S, &a, &b);
                     }
-                    while (__any_sync(0xffffffffu, bits != 0)) {
-                        uint32_t kk = 0;
-                        uint64_t n = 0, a = 0, b = 0;
-                        if (bits) {
-                            const uint32_t i = 32 * w + (uint32_t)(__ffs(bits) - 1);
-                            bits &= bits - 1;
-                            n = t_lo + i;
-                            const uint64_t s0 = tile[i], s1 = tile[i + 1];
-                            // bit-length bound first: s(n)s(n+1) < 2^lb, power of 2 included
-                            const int lb = (int)(bitlen64(s0) + bitlen64(s1) + ctz64(n + (n & 1))) - 1;
-                            if (lb > thr_lb) kk = exact_kinds(n, s0, s1, kinds, MODE, P.hash_S, &a, &b);
-                        }
-                        // warp-ballot compaction: one atomic per warp
-                        const uint32_t m = __ballot_sync(0xffffffffu, kk != 0);
-                        if (m) {
-                            unsigned long long wbase = 0;
-                            if (lane == 0) wbase = atomicAdd(&P.ctr->n_surv, (unsigned long long)__popc(m));
-                            wbase = __shfl_sync(0xffffffffu, wbase, 0);
-                            if (kk) {
-                                const unsigned long long at = wbase + __popc(m & ((1u << lane) - 1));
-                                if (at < P.surv_cap) {
-                                    Survivor sv;
-                                    sv.n = n;
-                                    sv.a = a;
-                                    sv.b = b;
-                                    sv.kinds = kk;
-                                    sv.iv = s_iv;
-                                    P.surv[at] = sv;
-                                } else {
-                                    atomicOr(&P.ctr->err, kErrSurvOverflow);
-                                }
-                                if (MODE == kModeSearch) {
-                                    if (kk & 1) atomicAdd(&P.ctr->surv1, 1ull);
-                                    if (kk & 2) atomicAdd(&P.ctr->surv2, 1ull);
-                                }
+                    // warp-ballot compaction: one atomic per warp
+                    const uint32_t m = __ballot_sync(0xffffffffu, kk != 0);
+                    if (m) {
+                        unsigned long long wbase = 0;
+                        if (lane == 0) wbase = atomicAdd(&P.ctr->n_surv, (unsigned long long)__popc(m));
+                        wbase = __shfl_sync(0xffffffffu, wbase, 0);
+                        if (kk) {
+                            const unsigned long long at = wbase + __popc(m & ((1u << lane) - 1));
+                            if (at < P.surv_cap) {
+                                Survivor sv;
+                                sv.n = n;
+                                sv.a = a;
+                                sv.b = b;
+                                sv.kinds = kk;
+                                sv.iv = s_iv;
+                                P.surv[at] = sv;
+                            } else {
+                                atomicOr(&P.ctr->err, kErrSurvOverflow);
+                            }
+                            if (MODE == kModeSearch) {
+                                if (kk & 1) atomicAdd(&P.ctr->surv1, 1ull);
+                                if (kk & 2) atomicAdd(&P.ctr->surv2, 1ull);
                             }
                         }
                     }
@@ -525,7 +512,6 @@ const void *sieve_fn_t(int threads) {
 }
 
 const void *sieve_fn(int mode, int threads) {
-    if (mode == kModeRad) return sieve_fn_t<kModeRad>(threads);
     if (mode == kModeHash) return sieve_fn_t<kModeHash>(threads);
     return sieve_fn_t<kModeSearch>(threads);
 }

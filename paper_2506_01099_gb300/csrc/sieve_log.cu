@@ -23,6 +23,7 @@
 // entries of the larger primes) and the exact 128-bit conditions.
 #include <algorithm>
 
+#include "bnx_exact.cuh"
 #include "bnx_internal.cuh"
 
 namespace bnx {
@@ -43,7 +44,6 @@ constexpr int kLogBucketCache = 512;
 // an entry on a tile boundary (x = L_tile of one tile, x = 0 of the next) is in both bins.
 constexpr uint32_t kMaxSegTiles = 64;
 constexpr uint32_t kHigh2 = 16;
-constexpr int kMaxSmallPrimes = 64;
 // Runs of dense strike rounds per warp (a warp's equal share of all dense rounds of a tile
 // touches at most every dense prime power once; for tiles up to 2^16 there are at most 21:
 // odd p^k <= 2^16/31 with k >= 2)
@@ -81,35 +81,6 @@ __host__ __device__ inline LogLayout log_layout(uint32_t tile_log2, uint32_t nsp
 template <int VB>
 __device__ __forceinline__ uint32_t pack_hit(uint2 h) {
     return (h.x << 12) | cache_weight<VB>(h.y);
-}
-
-struct SmallPrimes {
-    uint32_t n;
-    uint32_t p[kMaxSmallPrimes];
-    unsigned long long inv[kMaxSmallPrimes];  // p^-1 mod 2^64
-    unsigned long long lim[kMaxSmallPrimes];  // floor((2^64 - 1) / p)
-};
-
-// exact odd square part of the value v at offset o of its segment
-__device__ __noinline__ uint64_t sodd_exact(uint64_t v, uint32_t o, const SmallPrimes *sp, uint32_t sqrt_q,
-                                            const uint2 *bent, unsigned long long gb, unsigned long long ge) {
-    uint64_t y = v >> ctz64(v);
-    uint64_t s = 1;
-    for (uint32_t t = 0; t < sp->n; t++) {
-        const unsigned long long inv = sp->inv[t], lim = sp->lim[t];
-        if (y * inv <= lim) {  // p | y (exact-division test)
-            y *= inv;
-            while (y * inv <= lim) {
-                y *= inv;
-                s *= sp->p[t];
-            }
-        }
-    }
-    for (unsigned long long e = gb; e < ge; e++) {
-        const uint2 h = bent[e];
-        if (h.x == o && h.y > sqrt_q) s *= h.y;
-    }
-    return s;
 }
 
 // exact per-kind decision from the odd square parts of n and n+1
@@ -599,21 +570,7 @@ template <int MODE>
 __global__ void __launch_bounds__(256) k_cand(Plan P) {
     __shared__ SmallPrimes sprimes;
     const uint32_t tid = threadIdx.x, lane = tid & 31;
-    if (tid == 0) {
-        // distinct in-tile primes (their square is an in-tile prime power)
-        uint32_t c = 0;
-        for (uint32_t j = 0; j < P.n_spp && c < kMaxSmallPrimes; j++)
-            if (P.spp[j].k == 2) sprimes.p[c++] = P.spp[j].p;
-        sprimes.n = c;
-    }
-    __syncthreads();
-    for (uint32_t t = tid; t < sprimes.n; t += blockDim.x) {
-        const unsigned long long p = sprimes.p[t];
-        unsigned long long inv = p;  // Newton: each step doubles the correct low bits
-        for (int it = 0; it < 6; it++) inv *= 2ull - p * inv;
-        sprimes.inv[t] = inv;
-        sprimes.lim[t] = ~0ull / p;
-    }
+    load_small_primes(P, &sprimes);
     __syncthreads();
     const unsigned long long nc = min(P.ctr->n_cand, (unsigned long long)P.cand_cap);
     const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;

@@ -610,3 +610,23 @@ def test_same_rad_on_constructed_pairs(B, orc):
     bad = [(xs[i], ys[i], want[i]) for i in range(len(xs)) if bool(got[i]) != want[i]]
     assert not bad, bad[:5]
     assert sum(want) > 1000 and len(want) - sum(want) > 1000
+
+
+def test_rad_segment_square_parts_past_2p32(ctx, orc):
+    """Values whose odd square part passes 2^32 (the radical tile's 32-bit products give
+    way to an exact recomputation): windows around odd prime powers with exponent large
+    enough, and multiples of 3^21, against the oracle's trial division, rad and square
+    part both."""
+    centres = [3**22, 2 * 3**22, 4 * 3**23, 3**25, 7**13, 5**16, 11**11, 13**10, 17**9, 3**20 * 5**3,
+               25 * 3**21, 49 * 3**21, 121 * 3**21]
+    seen = 0
+    for c in centres:
+        lo = c - 700
+        rad, sq = gpu_rad(ctx, lo, 1401)
+        want = orc.rad_td_array(lo, 1401)
+        assert np.array_equal(rad, want), (c, int(np.nonzero(rad != want)[0][0]))
+        xs = np.arange(lo, lo + 1401, dtype=np.uint64)
+        assert np.array_equal(sq * rad, xs), c
+        odd_sq = [int(v) >> (int(v) & -int(v)).bit_length() - 1 if v else 0 for v in sq]
+        seen += sum(1 for v in odd_sq if v >= 1 << 32)
+    assert seen >= len(centres)  # every window holds at least its centre (odd square part > 2^32)
