@@ -40,11 +40,12 @@ KERNELS_PER_STEP = 11  # plan, bucket count, 3 scan kernels, bucket fill, sieve,
 # Strikes: sum over odd prime powers q = p^k, k >= 2, of 1/q
 # = sum_{p>=3} 1/(p(p-1)) = 0.2732 per integer, each an address step, a bound test and a
 # shared-memory reduction (3 ops).  Log tiles: the pair test of a word of VPW values is a
-# funnel shift, the pair add, the threshold add and the flag OR (4 ops per word), plus a
+# funnel shift, the pair add, the threshold add and the flag OR (4 ops per word; the u8 tile,
+# whose pair sums stay below 2^7, adds pair and threshold in one 3-input add: 3 ops), plus a
 # 16-byte load and a 16-byte clear per 16 bytes of tile.  The exact u64 tile: clear 1, strikes
 # as 64-bit multiplies (5 ops), 2-adic valuation 2, key and filter 10.
 STRIKE_OPS = 0.2732 * 3
-ALG_OPS_PER_INT = {3: STRIKE_OPS + 4 / 4 + 2 / 16,     # u8: 4 values per word, 16 per 16 bytes
+ALG_OPS_PER_INT = {3: STRIKE_OPS + 3 / 4 + 2 / 16,     # u8: 4 values per word, 16 per 16 bytes
                    2: STRIKE_OPS + 4 / 2 + 2 / 8,      # u16
                    0: STRIKE_OPS + 4 / 1 + 2 / 4,      # u32
                    1: 1 + 0.2732 * 5 + 2 + 10}         # exact u64 tile

@@ -206,15 +206,23 @@ int bnx_rad_segment_noalloc(uint64_t lo, uint64_t len, uint64_t *rad_out, uint64
  * smallest integer L with 2^L > p^(2^f) -- the bit length of p^(2^f) --
  * computed in integers by repeated squaring with upward rounding; it never
  * falls below the bit length and equals it unless a rounding tie intervenes.
- * Host code only (no GPU needed); 2 <= p < 2^32, f <= 16, else 0. */
+ * Host code only (no GPU needed); 2 <= p < 2^32, f <= 16, else 0.  The u16 and
+ * u32 tiles use it with F = 2^8 and 2^16. */
 uint32_t bnx_log_weight(uint64_t p, uint32_t frac_log2);
+
+/* The u8 tile's weight, in units of 4/5 bit (F = 5/4): ceil(bitlen(p^5) / 4),
+ * with p^5 computed exactly in 128-bit integers.  bitlen(p^5) > 5 log2 p, so the
+ * weight exceeds (5/4) log2 p.  At most 1.468 units per bit of p (p = 17), so a
+ * u8 value stays below 2^6 and a pair sum below 2^7 for n < 2^42.  Host code
+ * only; 2 <= p < 2^25, else 0. */
+uint32_t bnx_log_weight54(uint64_t p);
 
 /* For every prime p <= sqrt(max_hi) of the context's device table (ascending),
  * the weights the log tile `tile_kind` (0 = u32, 2 = u16, 3 = u8) adds, read
  * along the kernels' own code paths on the device: out[4i .. 4i+4) =
  * {p, in-tile strike weight, weight of a bucket hit through the shared-memory
  * cache, weight of a bucket hit read from global memory}, in units of 2^-16,
- * 2^-8 or 2^-1 bit.  `out` is a HOST buffer of 4 * cap uint32_t; *n_out is the
+ * 2^-8 or 4/5 bit.  `out` is a HOST buffer of 4 * cap uint32_t; *n_out is the
  * number of primes.  Blocking.  Errors: BNX_E_ARG, BNX_E_TRUNCATED, BNX_E_CUDA. */
 int bnx_log_weights(bnx_ctx *ctx, uint32_t tile_kind, uint32_t *out, size_t cap, size_t *n_out);
 

@@ -92,6 +92,7 @@ def lib(auto_build: bool = True):
             "bnx_rad_segment": ([vp, u64, u64, vp, vp, vp], i32),
             "bnx_rad_segment_noalloc": ([u64, u64, vp, vp, vp], i32),
             "bnx_log_weight": ([u64, u32], u32),
+            "bnx_log_weight54": ([u64], u32),
             "bnx_same_rad": ([P(u64), P(u64), sz, P(ctypes.c_uint8)], i32),
             "bnx_log_weights": ([vp, u32, P(u32), sz, P(sz)], i32),
             "bnx_search": ([vp, u64, u64, u32, P(bnx_pair), sz, P(sz)], i32),
@@ -197,6 +198,11 @@ def bnx_rad_segment_noalloc(lo: int, length: int, rad_out_ptr: int, sq_out_ptr: 
 def bnx_log_weight(p: int, frac_log2: int) -> int:
     """Smallest L with 2^L > p^(2^frac_log2), in integers (host only)."""
     return int(lib().bnx_log_weight(p, frac_log2))
+
+
+def bnx_log_weight54(p: int) -> int:
+    """The u8 tile's weight ceil(bitlen(p^5) / 4), units of 4/5 bit (host only)."""
+    return int(lib().bnx_log_weight54(p))
 
 
 def bnx_same_rad(x, y):

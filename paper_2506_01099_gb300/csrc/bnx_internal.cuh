@@ -71,18 +71,34 @@ __host__ __device__ inline uint32_t log_weight(uint64_t p, uint32_t f) {
     return (e << f) + k + 1;
 }
 
+// log_weight54(p) = ceil(bitlen(p^5) / 4), the u8 tile's weight in units of 4/5
+// bit: bitlen(p^5) = floor(5 log2 p) + 1 > 5 log2 p, so the weight exceeds
+// (5/4) log2 p.  p^5 is computed exactly in 128 bits (2 <= p < 2^25, else 0).
+__host__ __device__ inline uint32_t log_weight54(uint64_t p) {
+    if (p < 2 || p >= (1ull << 25)) return 0;
+    const unsigned __int128 p2 = (unsigned __int128)p * p;
+    const unsigned __int128 p5 = p2 * p2 * p;  // below 2^125
+    const uint64_t hi = (uint64_t)(p5 >> 64), lo = (uint64_t)p5;
+#ifdef __CUDA_ARCH__
+    const uint32_t bl = hi ? 128u - (uint32_t)__clzll((long long)hi) : 64u - (uint32_t)__clzll((long long)lo);
+#else
+    const uint32_t bl = hi ? 128u - (uint32_t)__builtin_clzll(hi) : 64u - (uint32_t)__builtin_clzll(lo);
+#endif
+    return (bl + 3) / 4;
+}
+
 // Weight of an in-tile strike (q = p^k <= Q) in the tile's units: VB bytes per
-// tile value; units of 2^-1 bit (VB = 1), 2^-8 (VB = 2) or 2^-16 (VB = 4).
+// tile value; units of 4/5 bit (VB = 1), 2^-8 (VB = 2) or 2^-16 (VB = 4).
 template <int VB>
 __host__ __device__ inline uint32_t tile_weight(uint64_t p) {
-    return log_weight(p, VB == 1 ? 1u : VB == 2 ? 8u : 16u);
+    return VB == 1 ? log_weight54(p) : log_weight(p, VB == 2 ? 8u : 16u);
 }
 // The 12-bit weight field of a bucket entry cached in shared memory: the u8
-// tile's own weight (at most 2 * 21 + 1 for p < 2^21), else the weight in
-// units of 2^-7 bit (below 2^12 for p < 2^21), scaled up by cache_to_tile.
+// tile's own weight (at most 28 for p < 2^22), else the weight in units of
+// 2^-7 bit (below 2^12 for p < 2^21), scaled up by cache_to_tile.
 template <int VB>
 __host__ __device__ inline uint32_t cache_weight(uint64_t p) {
-    return VB == 1 ? log_weight(p, 1) : log_weight(p, 7);
+    return VB == 1 ? log_weight54(p) : log_weight(p, 7);
 }
 template <int VB>
 __host__ __device__ inline uint32_t cache_to_tile(uint32_t w) {

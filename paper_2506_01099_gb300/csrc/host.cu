@@ -831,6 +831,8 @@ extern "C" {
 
 uint32_t bnx_log_weight(uint64_t p, uint32_t frac_log2) { return log_weight(p, frac_log2); }
 
+uint32_t bnx_log_weight54(uint64_t p) { return log_weight54(p); }
+
 int bnx_same_rad(const uint64_t *x, const uint64_t *y, size_t n, uint8_t *out) {
     if (n == 0) return BNX_OK;
     if (!x || !y || !out) return fail(BNX_E_ARG, "NULL argument");

@@ -1,11 +1,11 @@
 // Log-domain tile sieve for the search and hash modes (the default).
 //
 // The tile holds, per value x, L(x) = the sum of w(p) over the prime-power
-// strikes at x, where w(p) >= F log2 p in the tile's fixed-point scale F (2^16
-// for u32 values, 2^8 for u16, 2 for u8): the weights of bnx_internal.cuh, the
-// bit length of p^F computed in integers (no floating point decides anything
-// here).  So L(x) is an upper bound of F log2 s_odd(x), s_odd(x) being the odd
-// part of x / rad(x).  Strikes are 32-bit shared-memory reductions (no read-modify-write
+// strikes at x, where w(p) >= F log2 p in the tile's units per bit F (2^16 for
+// u32 values, 2^8 for u16, 5/4 for u8): the weights of bnx_internal.cuh, bit
+// lengths of powers of p computed in integers (no floating point decides
+// anything here).  So L(x) is an upper bound of F log2 s_odd(x), s_odd(x) being
+// the odd part of x / rad(x).  Strikes are 32-bit shared-memory reductions (no read-modify-write
 // loop: addition commutes, so strikes of different prime powers at one x need
 // no ordering).  Algorithm 1 (Sec. 2.1) still decides which x a prime power
 // touches; only what is recorded there changes.
@@ -118,15 +118,18 @@ struct LogMinBlocks {
 //    L(x) <= 2^8 log2 s_odd(x) + (strikes at x) < 42 * 2^8 + 42 < 2^14, and a pair sum
 //    L(n) + L(n+1) < 2^15, so a strike's addition of lg << 16*(x&1) never carries into
 //    the neighbour, nor does a pair sum.
-//  VB = 1: 8 bits with 1 fractional bit (half-bit units), four values per word.  w(p)
-//    = floor(2 log2 p) + 1 is at most 4/log2(3) = 2.52 units per bit of p (p = 3 is the
-//    worst; a prime p > 2^7 takes at most 2 + 1/7 units per bit), so for x < 2^42
-//    L(x) <= 2.52 * 41 < 2^7 and a pair sum L(n) + L(n+1) <= 2.52 * 84 < 2^8: neither a
-//    strike nor a pair sum carries into the neighbouring byte.
+//  VB = 1: 8 bits in units of 4/5 bit (F = 5/4), four values per word.  w(p) =
+//    ceil(bitlen(p^5) / 4) > (5/4) log2 p is at most 1.468 units per bit of p (p = 17,
+//    w = 6, is the worst over all primes below 2^22).  s_odd(x) <= x / 3 whenever it
+//    exceeds 1, so for x < 2^42, L(x) <= 1.468 (42 - log2 3) < 60 and a pair sum
+//    L(n) + L(n+1) < 120 < 2^7: no strike, pair sum or threshold add below carries
+//    into the neighbouring byte.
 template <int MODE, int NT, int VB>
 __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(Plan P) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    constexpr uint32_t FS = VB == 4 ? 65536u : VB == 2 ? 256u : 2u;  // fixed-point scale of L
+    // units of L per bit: FN / FD
+    constexpr uint32_t FN = VB == 4 ? 65536u : VB == 2 ? 256u : 5u;
+    constexpr uint32_t FD = VB == 1 ? 4u : 1u;
     constexpr uint32_t VSH = VB == 4 ? 0u : VB == 2 ? 1u : 2u;       // value index >> VSH = word index
     constexpr uint32_t VPW = 1u << VSH;                             // values per word
     constexpr uint32_t VBITS = 8u * VB;
@@ -333,7 +336,9 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
                 const int clog = (int)flog2_64(S2) + ((S2 & (S2 - 1)) ? 1 : 0);
                 lthr = (int)flog2_64(t_lo) + (int)flog2_64(t_lo + 1) - clog;  // need log2 P >= log2(n(n+1)/2S)
             }
-            T = ((int64_t)lthr - (int64_t)(kHigh2 - 2)) * FS;
+            // n is rejected when L(n) + L(n+1) < F (lthr - (M - 2)), i.e. below its ceiling T
+            const int64_t tb = (int64_t)lthr - (int64_t)(kHigh2 - 2);
+            T = tb <= 0 ? tb : (tb * FN + FD - 1) / FD;
             const bool all_cand = T <= 0;
             const uint32_t T32 = all_cand ? 0u : (uint32_t)T;
             __syncthreads();
@@ -430,15 +435,69 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
                 const uint32_t off = sdesc[j].z, lm = slmod[j];
                 sdesc[j].z = off >= lm ? off - lm : off + sdesc[j].x - lm;
             }
-            // epilogue: G consecutive n per thread (4 u32 values per 16-byte load; 16 u16 or 32 u8
-            // values per two 16-byte loads)
+            // epilogue: G n per thread (4 u32 values per 16-byte load; 16 u16 or 32 u8 values per two
+            // 16-byte loads), consecutive except in the u8 tile (below)
             constexpr uint32_t M2 = 1u << kHigh2;
             constexpr uint32_t G = VB == 4 ? 4u : VB == 2 ? 16u : 32u;
-            const uint32_t ngroups = (tl + G - 1) / G;
+            // u8 tile: a warp reads a block of 1024 values, lane l the 16-byte chunks l and 32 + l
+            // (values 16 l .. 16 l + 15 and 512 + 16 l .. 512 + 16 l + 15 of the block), so that both
+            // 16-byte loads of the warp are free of bank conflicts; bit u of the candidate mask is
+            // value ibase + uoff(u)
+            constexpr bool kSplit = VB == 1;
+            const uint32_t ngroups = kSplit ? ((tl + 1023u) >> 10) << 5 : (tl + G - 1) / G;
+            auto uoff = [](uint32_t u) -> uint32_t { return kSplit && u >= 16u ? u + 496u : u; };
+            // offset of the first multiple of 2^M at or after t_lo (the others in the tile are at
+            // sp + k 2^M)
+            const uint32_t sp = (0u - (uint32_t)t_lo) & (M2 - 1);
+            // the exact power of 2 of P for a candidate at tile offset i, and warp-ballot compaction
+            // of those whose bound still reaches the threshold into the list of the exact check
+            // (k_cand: about 2 per 2^23 integers near 2^40); the whole warp calls it
+            auto consider = [&](bool has, uint32_t i) {
+                bool defer = false;
+                uint64_t n = 0;
+                if (has) {
+                    n = t_lo + i;
+                    const uint32_t e2 = ctz64(n + (n & 1)) - 1;  // power of 2 in P
+                    const uint32_t L0 = (tile[i >> VSH] >> ((i & (VPW - 1)) * VBITS)) & VMASK;
+                    const uint32_t L1 = (tile[(i + 1) >> VSH] >> (((i + 1) & (VPW - 1)) * VBITS)) & VMASK;
+                    // log2 P <= (L0 + L1) / F + e2 must reach `need`
+                    const int64_t ub = (int64_t)(L0 + L1) * FD + (int64_t)e2 * FN;
+                    int need;
+                    if (MODE == kModeSearch) {
+                        need = (int)flog2_64(n + 1) - 1;
+                    } else {
+                        const uint64_t S2 = 2 * P.hash_S;
+                        need = (int)flog2_64(n) + (int)flog2_64(n + 1) - (int)flog2_64(S2) - ((S2 & (S2 - 1)) ? 1 : 0);
+                    }
+                    defer = ub >= (int64_t)need * FN;
+                }
+                const uint32_t m = __ballot_sync(0xffffffffu, defer);
+                if (m) {
+                    unsigned long long wbase = 0;
+                    if (lane == 0) wbase = atomicAdd(&P.ctr->n_cand, (unsigned long long)__popc(m));
+                    wbase = __shfl_sync(0xffffffffu, wbase, 0);
+                    if (defer) {
+                        const unsigned long long at = wbase + __popc(m & ((1u << lane) - 1));
+                        if (at < P.cand_cap) {
+                            Cand cd;
+                            cd.n = n;
+                            cd.b0 = b0;
+                            cd.nb = (uint32_t)(b1 - b0);
+                            cd.o = t0 + i;
+                            cd.kinds = kinds;
+                            cd.iv = ivi;
+                            P.cand[at] = cd;
+                        } else {
+                            atomicOr(&P.ctr->err, kErrCandOverflow);
+                        }
+                    }
+                }
+            };
             const uint4 *t4 = reinterpret_cast<const uint4 *>(tile);
             for (uint32_t base = 0; base < ngroups; base += NT) {
                 const uint32_t g = base + tid;
-                uint32_t cm = 0;  // candidates among the group's n (bit u: n = t_lo + G*g + u)
+                const uint32_t ibase = kSplit ? ((g >> 5) << 10) + ((g & 31u) << 4) : G * g;
+                uint32_t cm = 0;  // candidates among the group's n (bit u: n = t_lo + ibase + uoff(u))
                 if (g < ngroups) {
                     uint32_t ss[G];
                     bool logc;
@@ -451,14 +510,22 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
                         ss[3] = v.w + w;
                         logc = max(max(ss[0], ss[1]), max(ss[2], ss[3])) >= T32;
                     } else {
-                        const uint4 v = t4[2 * g], v2 = t4[2 * g + 1];
-                        const uint32_t w = tile[8 * g + 8];
-                        // packed pair sums: field i of pw[k] is L(VPW k + i) + L(VPW k + i + 1)
+                        // u8: the chunks at bytes ibase and ibase + 512, and the word after each
+                        const unsigned char *tb = reinterpret_cast<const unsigned char *>(tile) + ibase;
+                        const uint4 v = kSplit ? *reinterpret_cast<const uint4 *>(tb) : t4[2 * g];
+                        const uint4 v2 = kSplit ? *reinterpret_cast<const uint4 *>(tb + 512) : t4[2 * g + 1];
+                        const uint32_t w = kSplit ? *reinterpret_cast<const uint32_t *>(tb + 528) : tile[8 * g + 8];
+                        // packed pair sums: field i of pw[k] is L(j) + L(j + 1) for the group's value j =
+                        // VPW k + i (u8: j = uoff(4 k + i))
                         uint32_t pw[8];
                         pw[0] = v.x + __funnelshift_r(v.x, v.y, VBITS);
                         pw[1] = v.y + __funnelshift_r(v.y, v.z, VBITS);
                         pw[2] = v.z + __funnelshift_r(v.z, v.w, VBITS);
-                        pw[3] = v.w + __funnelshift_r(v.w, v2.x, VBITS);
+                        if constexpr (kSplit) {
+                            pw[3] = v.w + __funnelshift_r(v.w, *reinterpret_cast<const uint32_t *>(tb + 16), VBITS);
+                        } else {
+                            pw[3] = v.w + __funnelshift_r(v.w, v2.x, VBITS);
+                        }
                         pw[4] = v2.x + __funnelshift_r(v2.x, v2.y, VBITS);
                         pw[5] = v2.y + __funnelshift_r(v2.y, v2.z, VBITS);
                         pw[6] = v2.z + __funnelshift_r(v2.z, v2.w, VBITS);
@@ -470,15 +537,13 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
                             logc = (((pw[0] + K) | (pw[1] + K) | (pw[2] + K) | (pw[3] + K) | (pw[4] + K) |
                                      (pw[5] + K) | (pw[6] + K) | (pw[7] + K)) & 0x80008000u) != 0u;
                         } else {
-                            // a byte pair sum s is below 2^8.  With T' = min(T, 127) and K = 128 - T',
-                            // s >= T' sets bit 7 of s + K (plus a carry from the byte below), unless
-                            // that sum reaches 2^8 -- and then s >= 128 + T' - 1 has bit 7 set itself.
-                            // So bit 7 of s | (s + K) is set whenever s >= T; carries between bytes
-                            // only add flags, and flagged values are re-checked one by one below.
+                            // a byte pair sum s is below 2^7: with T' = min(T, 127) and K = 128 - T',
+                            // s + K stays below 2^8 and has bit 7 set exactly when s >= T' (and s >= T
+                            // needs s >= T')
                             const uint32_t K = (0x80u - (T32 < 0x7fu ? T32 : 0x7fu)) * 0x01010101u;
                             uint32_t acc = 0;
 #pragma unroll
-                            for (uint32_t u = 0; u < 8; u++) acc |= pw[u] | (pw[u] + K);
+                            for (uint32_t u = 0; u < 8; u++) acc |= pw[u] + K;
                             logc = (acc & 0x80808080u) != 0u;
                         }
 #pragma unroll
@@ -486,15 +551,17 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
 #pragma unroll
                             for (uint32_t b = 0; b < VPW; b++) ss[VPW * u + b] = (pw[u] >> (b * VBITS)) & VMASK;
                     }
-                    const uint32_t n0 = (uint32_t)(t_lo + G * g);  // low 32 bits suffice modulo 2^M
-                    // does [n0, n0 + G] hold a multiple of 2^M?
-                    const bool hi2 = ((n0 + G) & (M2 - 1)) <= G;
+                    const uint32_t n0 = (uint32_t)(t_lo + ibase);  // low 32 bits suffice modulo 2^M
+                    // does [n0, n0 + G] hold a multiple of 2^M?  (u8: the n next to one are taken
+                    // after the group loop)
+                    const bool hi2 = !kSplit && ((n0 + G) & (M2 - 1)) <= G;
                     if (all_cand || logc) {
 #pragma unroll
                         for (uint32_t u = 0; u < G; u++) {
-                            const uint32_t nl = n0 + u;
+                            const uint32_t nl = n0 + uoff(u);
                             const bool h = ((nl & (M2 - 1)) == 0) || (((nl + 1) & (M2 - 1)) == 0);
-                            if ((all_cand || ss[u] >= T32 || h) && G * g + u < tl) cm |= 1u << u;
+                            const bool pick = kSplit ? (all_cand || ss[u] >= T32) && !h : all_cand || ss[u] >= T32 || h;
+                            if (pick && ibase + uoff(u) < tl) cm |= 1u << u;
                         }
                     } else if (hi2) {
                         // about one group per tile: only the n next to the multiple n0 + u0 of 2^M
@@ -506,53 +573,22 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
                         if (left < G) cm &= (1u << left) - 1u;
                     }
                 }
-                // candidates whose bound, with the exact power of 2 of P, still reaches the
-                // threshold go to the exact check (k_cand): about 2 per 2^23 integers near 2^40
                 while (__any_sync(0xffffffffu, cm != 0)) {
-                    bool defer = false;
-                    uint64_t n = 0;
                     uint32_t i = 0;
-                    if (cm) {
+                    const bool has = cm != 0;
+                    if (has) {
                         const uint32_t u = (uint32_t)(__ffs(cm) - 1);
                         cm &= cm - 1;
-                        i = G * g + u;
-                        n = t_lo + i;
-                        const uint32_t e2 = ctz64(n + (n & 1)) - 1;  // power of 2 in P
-                        const uint32_t L0 = (tile[i >> VSH] >> ((i & (VPW - 1)) * VBITS)) & VMASK;
-                        const uint32_t L1 = (tile[(i + 1) >> VSH] >> (((i + 1) & (VPW - 1)) * VBITS)) & VMASK;
-                        const int64_t ub = (int64_t)(L0 + L1) + (int64_t)e2 * FS;
-                        int need;  // log2 P <= ub / FS must reach it
-                        if (MODE == kModeSearch) {
-                            need = (int)flog2_64(n + 1) - 1;
-                        } else {
-                            const uint64_t S2 = 2 * P.hash_S;
-                            need = (int)flog2_64(n) + (int)flog2_64(n + 1) - (int)flog2_64(S2) -
-                                   ((S2 & (S2 - 1)) ? 1 : 0);
-                        }
-                        defer = ub >= (int64_t)need * FS;
+                        i = ibase + uoff(u);
                     }
-                    const uint32_t m = __ballot_sync(0xffffffffu, defer);  // warp-ballot compaction
-                    if (m) {
-                        unsigned long long wbase = 0;
-                        if (lane == 0) wbase = atomicAdd(&P.ctr->n_cand, (unsigned long long)__popc(m));
-                        wbase = __shfl_sync(0xffffffffu, wbase, 0);
-                        if (defer) {
-                            const unsigned long long at = wbase + __popc(m & ((1u << lane) - 1));
-                            if (at < P.cand_cap) {
-                                Cand cd;
-                                cd.n = n;
-                                cd.b0 = b0;
-                                cd.nb = (uint32_t)(b1 - b0);
-                                cd.o = t0 + i;
-                                cd.kinds = kinds;
-                                cd.iv = ivi;
-                                P.cand[at] = cd;
-                            } else {
-                                atomicOr(&P.ctr->err, kErrCandOverflow);
-                            }
-                        }
-                    }
+                    consider(has, i);
                 }
+            }
+            if (kSplit && warp == 0) {
+                // u8: the n next to a multiple of 2^M (their power of 2 may exceed 2^(M-2)), at the
+                // tile offsets sp - 1, sp, sp + 2^M - 1 and sp + 2^M that lie in [0, tl)
+                const uint32_t i = sp + (lane >> 1) * M2 + (lane & 1u) - 1u;
+                consider(lane < 4u && i < tl, i);
             }
         }
         // every thread has read s_seg .. s_b1 and is done with the bins (a barrier of the tile
