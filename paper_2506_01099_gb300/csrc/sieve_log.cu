@@ -223,6 +223,9 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
             s_nsparse = incw <= P.n_sched ? incw : 0u;  // n_sched always covers them
             if (incw > P.n_sched && blockIdx.x == 0) atomicOr(&P.ctr->err, kErrSchedule);
         }
+        // every packed slot after a warp's first pass (a dependent shared-load chain and a
+        // reduction) counts against that warp's share of the dense rounds
+        const uint32_t ns_all = __shfl_sync(0xffffffffu, incw <= P.n_sched ? incw : 0u, 31);
         // lane w < NT/32 lists the runs of warp w.  The shares are equal in estimated cost, not
         // in rounds: a run costs about kRunSetup instructions to set up and kRoundCost per
         // round, and the prime powers with few rounds (and so many runs) come last.  Round k of
@@ -235,7 +238,28 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
                 const int r = (int)sdesc[j].w;
                 if (r > 1) T += kRunSetup + r * kRoundCost;
             }
-            const int b = (int)((int64_t)T * lane / nwarps), e = (int)((int64_t)T * (lane + 1) / nwarps);
+            // warp w takes the rounds whose cost position lies in [B_w, B_(w+1)), B_w the running
+            // maximum of (T + E) w / nwarps - (extra cost of warps below w), clamped to [0, T]:
+            // contiguous, non-overlapping shares that cover [0, T) whatever the extra costs
+            constexpr int kSlotPass = 40;
+            auto extra = [&](uint32_t w) -> int {
+                int c = 0;
+                for (uint32_t p = NT + 32 * w; p < ns_all; p += NT) c++;
+                return c * kSlotPass;
+            };
+            int E = 0;
+            for (uint32_t v = 0; v < nwarps; v++) E += extra(v);
+            auto bound = [&](uint32_t w) -> int {  // B_w
+                int best = 0, pre = 0;
+                for (uint32_t v = 0; v <= w && v <= nwarps; v++) {
+                    int r = v == nwarps ? T : (int)((int64_t)(T + E) * v / nwarps) - pre;
+                    r = r < 0 ? 0 : r > T ? T : r;
+                    best = r > best ? r : best;
+                    if (v < nwarps) pre += extra(v);
+                }
+                return best;
+            };
+            const int b = bound(lane), e = bound(lane + 1);
             auto first_at = [&](int pos, int cs, int r) -> int {  // first round k sitting at or after pos
                 const int x = 2 * (pos - cs - kRunSetup) - kRoundCost;  // in half-units
                 const int k = x <= 0 ? 0 : (x + 2 * kRoundCost - 1) / (2 * kRoundCost);
@@ -379,6 +403,7 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
                     sv0 = d.y << ((x & (VPW - 1)) * VBITS);
                 }
             }
+            if (sp0) red_add_shared(sa0, sv0);
             // this warp's runs of dense rounds
             for (uint32_t k = 0; k < nruns; k++) {
                 const uint32_t run = s_runs[warp][k];
@@ -405,7 +430,6 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
                 }
             }
             // packed slots of the single-round prime powers
-            if (sp0) red_add_shared(sa0, sv0);
             for (uint32_t sl = warp * 32 + lane + NT; sl < ((nsparse + 31) & ~31u); sl += NT) {
                 if (sl < nsparse) {
                     const uint32_t e = sched[sl];
