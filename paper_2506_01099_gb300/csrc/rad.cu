@@ -96,6 +96,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_rad(Plan P) {
     constexpr uint32_t nwarps = NT / 32;
     const uint32_t k = *P.n_iv;
     const unsigned long long total_segs = min(P.ctr->total_segs, (unsigned long long)P.seg_cap);
+    const bool pair_ok = ((reinterpret_cast<uintptr_t>(P.rad_out) | reinterpret_cast<uintptr_t>(P.sq_out)) & 15u) == 0;
 
     for (uint32_t j = tid; j < nspp; j += NT) {
         const SmallPP e = P.spp[j];
@@ -209,20 +210,40 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_rad(Plan P) {
                 soff[j] = off >= lm ? off - lm : off + sq[j] - lm;
             }
             // the values of this tile (not its halo): rad and the square part
-            for (uint32_t i = tid; i < tl; i += NT) {
+            auto finish = [&](uint32_t i, uint64_t *r, uint64_t *q) {  // value t_lo + i
                 const uint64_t x = t_lo + i;
-                const uint64_t gi = x - P.rad_lo;
+                const uint32_t tz = (uint32_t)(__ffsll((long long)x) - 1);
+                const uint64_t xo = x >> tz;
+                uint64_t so = tile[i];
+                if (so == 0) so = sodd_exact(x, t0 + i, &sprimes, P.sqrt_q, P.bent, b0, b1);  // past 2^32
+                uint64_t inv;
+                if (so < 256) inv = s_inv[so >> 1];
+                else inv = inv64(so);
+                const uint64_t ro = xo * inv;  // = x_odd / s, exactly
+                *r = tz ? ro << 1 : ro;
+                *q = so << (tz ? tz - 1 : 0);
+            };
+            // pairs of values with one 16-byte store per output: the output index of value
+            // t_lo + i is t_lo - rad_lo + i, and t_lo - rad_lo is even (segments and tiles
+            // start at even offsets), so an even i starts a 16-byte aligned pair when the
+            // outputs are 16-byte aligned; otherwise (and for a ragged end) one value at a time
+            const uint64_t g0 = t_lo - P.rad_lo;
+            const bool vec = pair_ok && g0 < P.rad_len && (g0 & 1) == 0;
+            const uint32_t tv = vec ? (uint32_t)min((uint64_t)tl, P.rad_len - g0) & ~1u : 0u;
+            for (uint32_t i = 2 * tid; i < tv; i += 2 * NT) {
+                uint64_t r0, q0, r1, q1;
+                finish(i, &r0, &q0);
+                finish(i + 1, &r1, &q1);
+                *reinterpret_cast<ulonglong2 *>(P.rad_out + g0 + i) = make_ulonglong2(r0, r1);
+                if (P.sq_out) *reinterpret_cast<ulonglong2 *>(P.sq_out + g0 + i) = make_ulonglong2(q0, q1);
+            }
+            for (uint32_t i = tv + tid; i < tl; i += NT) {
+                const uint64_t gi = t_lo + i - P.rad_lo;
                 if (gi < P.rad_len) {
-                    const uint32_t tz = (uint32_t)(__ffsll((long long)x) - 1);
-                    const uint64_t xo = x >> tz;
-                    uint64_t so = tile[i];
-                    if (so == 0) so = sodd_exact(x, t0 + i, &sprimes, P.sqrt_q, P.bent, b0, b1);  // past 2^32
-                    uint64_t inv;
-                    if (so < 256) inv = s_inv[so >> 1];
-                    else inv = inv64(so);
-                    const uint64_t ro = xo * inv;  // = x_odd / s, exactly
-                    P.rad_out[gi] = tz ? ro << 1 : ro;
-                    if (P.sq_out) P.sq_out[gi] = so << (tz ? tz - 1 : 0);
+                    uint64_t r, q;
+                    finish(i, &r, &q);
+                    P.rad_out[gi] = r;
+                    if (P.sq_out) P.sq_out[gi] = q;
                 }
             }
         }
