@@ -210,11 +210,11 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_rad(Plan P) {
                 soff[j] = off >= lm ? off - lm : off + sq[j] - lm;
             }
             // the values of this tile (not its halo): rad and the square part
-            auto finish = [&](uint32_t i, uint64_t *r, uint64_t *q) {  // value t_lo + i
+            auto finish = [&](uint32_t i, uint32_t s32, uint64_t *r, uint64_t *q) {  // value t_lo + i, tile[i]
                 const uint64_t x = t_lo + i;
                 const uint32_t tz = (uint32_t)(__ffsll((long long)x) - 1);
                 const uint64_t xo = x >> tz;
-                uint64_t so = tile[i];
+                uint64_t so = s32;
                 if (so == 0) so = sodd_exact(x, t0 + i, &sprimes, P.sqrt_q, P.bent, b0, b1);  // past 2^32
                 uint64_t inv;
                 if (so < 256) inv = s_inv[so >> 1];
@@ -232,8 +232,9 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_rad(Plan P) {
             const uint32_t tv = vec ? (uint32_t)min((uint64_t)tl, P.rad_len - g0) & ~1u : 0u;
             for (uint32_t i = 2 * tid; i < tv; i += 2 * NT) {
                 uint64_t r0, q0, r1, q1;
-                finish(i, &r0, &q0);
-                finish(i + 1, &r1, &q1);
+                const uint2 s2 = *reinterpret_cast<const uint2 *>(tile + i);  // i even: 8-byte aligned
+                finish(i, s2.x, &r0, &q0);
+                finish(i + 1, s2.y, &r1, &q1);
                 *reinterpret_cast<ulonglong2 *>(P.rad_out + g0 + i) = make_ulonglong2(r0, r1);
                 if (P.sq_out) *reinterpret_cast<ulonglong2 *>(P.sq_out + g0 + i) = make_ulonglong2(q0, q1);
             }
@@ -241,7 +242,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_rad(Plan P) {
                 const uint64_t gi = t_lo + i - P.rad_lo;
                 if (gi < P.rad_len) {
                     uint64_t r, q;
-                    finish(i, &r, &q);
+                    finish(i, tile[i], &r, &q);
                     P.rad_out[gi] = r;
                     if (P.sq_out) P.sq_out[gi] = q;
                 }
