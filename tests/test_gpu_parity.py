@@ -67,6 +67,36 @@ def test_rad_segment_bit_exact(ctx, orc, lo, length):
     assert np.array_equal(sq * rad, xs)
 
 
+def test_rad_segment_unaligned_outputs(ctx, orc):
+    """The kernel writes two values per 16-byte store when both output pointers are 16-byte
+    aligned, and one value at a time otherwise: output pointers 8 bytes past a 16-byte
+    boundary (one or both, and the radical alone) give the same values as aligned ones,
+    which equal the oracle's trial-division radicals."""
+    import torch
+
+    stream = torch.cuda.current_stream().cuda_stream
+    for lo, length in ((2**40 - 2**13, 2**14 + 3), (3**25 - 3001, 6001), (1, 70_000)):
+        want = orc.rad_td_array(lo, length)
+        rad_a, sq_a = gpu_rad(ctx, lo, length)
+        assert np.array_equal(rad_a, want)
+        for shift_rad, shift_sq in ((1, 1), (0, 1), (1, 0)):
+            rb = torch.zeros(length + 2, dtype=torch.int64, device="cuda")
+            qb = torch.zeros(length + 2, dtype=torch.int64, device="cuda")
+            ctx.rad_segment(lo, length, rb.data_ptr() + 8 * shift_rad, qb.data_ptr() + 8 * shift_sq, stream)
+            torch.cuda.synchronize()
+            r = rb.cpu().numpy().view(np.uint64)
+            q = qb.cpu().numpy().view(np.uint64)
+            assert np.array_equal(r[shift_rad:shift_rad + length], want), (lo, shift_rad, shift_sq)
+            assert np.array_equal(q[shift_sq:shift_sq + length], sq_a), (lo, shift_rad, shift_sq)
+            # nothing written outside the outputs
+            assert r[length + shift_rad:].sum() == 0 and r[:shift_rad].sum() == 0
+            assert q[length + shift_sq:].sum() == 0 and q[:shift_sq].sum() == 0
+        rb = torch.zeros(length + 1, dtype=torch.int64, device="cuda")
+        ctx.rad_segment(lo, length, rb.data_ptr() + 8, None, stream)
+        torch.cuda.synchronize()
+        assert np.array_equal(rb.cpu().numpy().view(np.uint64)[1:], want), lo
+
+
 def test_rad_segment_large_sampled(ctx, orc):
     """A 2^27-value segment at 2^40 (many queue segments): sampled windows vs trial division."""
     lo, length = 2**40 + 12345, 1 << 27
