@@ -143,6 +143,25 @@ def test_tunings_agree(B, orc, tune):
         assert c.stats()["hash_keys"] == orc.hash_keys(1 << 20)
 
 
+@pytest.mark.parametrize("tune", [dict(tile_kind=3), dict(tile_kind=3, tile_log2=16, seg_tiles=2, threads=512),
+                                  dict(tile_kind=2, tile_log2=15, seg_tiles=32), dict(tile_kind=1)])
+def test_neighbours_of_2p16_multiples_at_tile_edges(B, orc, tune):
+    """n next to a multiple of 2^16 are always candidates (their power of 2 can exceed the
+    log bound's 2^14).  n = 2^40 - 1 (rad(n) rad(n+1) ~ 2^41/5) survives the filters of both
+    kinds and sits on a tile edge here: a tile of 2^16 values starting at a multiple of 2^16
+    holds two multiples, and its last value is such an n.  Survivor counts and pairs equal
+    the oracle's."""
+    windows = [(2**40 - 2**16, 2**40 + 2**16), (2**40 - 2**17 + 1, 2**40 + 1), (2**40 - 1, 2**40 + 1),
+               (2**40 - 2**16, 2**40), (2**40, 2**40 + 3)]
+    with B.Context(0, max_hi=1 << 41) as c:
+        c.set_tune(**tune)
+        for lo, hi in windows:
+            assert c.search(lo, hi) == orc.pairs_crt(lo, hi), (lo, hi)
+            st = c.stats()
+            assert (st["survivors1"], st["survivors2"]) == orc.filter_counts(lo, hi), (lo, hi)
+    assert orc.filter_counts(2**40 - 1, 2**40) == (1, 1) and orc.filter_counts(2**40, 2**40 + 1) == (0, 0)
+
+
 def test_search_c1_full(ctx, orc):
     """All n < 2^24, both kinds: equals the oracle and Theorem 1 (25 pairs)."""
     got = ctx.search(1, 1 << 24)
