@@ -311,10 +311,11 @@ int bnx_batch(bnx_ctx *ctx, const bnx_interval *iv, size_t k, bnx_pair *out, siz
 typedef struct {
     uint32_t max_active;      /* requests on the device at once (slots, 1 .. 2^24) */
     uint32_t pad;
-    uint64_t slice;           /* integers of each active request per iteration: at least
-                                 slice, and an equal share of slice * max_active when
-                                 fewer than max_active requests are active (any value
-                                 >= 1; a slice beyond a request's end takes the rest) */
+    uint64_t slice;           /* an iteration runs as many integers as an equal share eq
+                                 of slice * max_active (at least slice per request)
+                                 would: a request with at most eq left finishes, every
+                                 other one gets slice, and the rest go to the oldest
+                                 requests first (any value >= 1) */
     uint64_t mem_budget;      /* bytes of device workspace the loop may hold (0: 90% of
                                  the HBM free at start); the context's prime tables are
                                  not counted */
@@ -336,9 +337,12 @@ typedef struct {
  *  - admits waiting requests in arrival order while a slot is free and an
  *    iteration giving every admitted request `slice` integers fits the budget
  *    (otherwise the request waits for memory);
- *  - takes the next slice of every active request (shortened, down to one
- *    queue segment, until the iteration's workspace fits the budget) and runs
- *    all of them as one batched pipeline, the workspace sized under the budget.
+ *  - takes the next slice of every active request (the requests that fit their
+ *    equal share finish; the others get `slice`, and the rest of the iteration
+ *    goes to the oldest first; the extra is cut, then the per-request slice down
+ *    to one queue segment, until the iteration's workspace fits the budget) and
+ *    runs all of them as one batched pipeline, the workspace sized under the
+ *    budget.
  * So the budget bounds the device memory the loop holds.
  * Errors: BNX_E_ARG, BNX_E_STATE (already running), BNX_E_NOMEM, BNX_E_CUDA. */
 int bnx_server_start(bnx_ctx *ctx, const bnx_server_cfg *cfg);

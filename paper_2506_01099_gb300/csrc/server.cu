@@ -8,12 +8,17 @@
 //   2. cuts the next slice of every active request and runs all slices as one
 //      batched pipeline (one persistent sieve launch over the shared queue), so
 //      the work of requests that arrived at different times overlaps on the GPU.
-//      An iteration covers up to slice * max_active integers, shared equally by the
-//      active requests (at least `slice` each): a request that runs alone or with
-//      few others advances in long slices, and with a full set each gets `slice`.
-//      The slices are shortened (down to one queue segment) until the iteration's
-//      workspace fits the budget, and the workspace is sized under the same budget,
-//      so the budget bounds the device memory the loop holds;
+//      An iteration covers as many integers as an equal share eq of slice * max_active
+//      (at least `slice` per request) would: a request with at most eq left finishes
+//      in it, as with equal shares; every other active request gets `slice`, and the
+//      rest go to those in order of arrival, so that a long request that is the
+//      oldest gets most of the GPU (close to first come, first served) instead of an
+//      equal share that stretches it over many iterations.  Iterations stay as long
+//      as with equal shares.
+//      While the iteration's workspace exceeds the budget the extra share is halved,
+//      then the per-request `slice` (down to one queue segment); the workspace is
+//      sized under the same budget, so the budget bounds the device memory the loop
+//      holds;
 //   3. appends each slice's pairs to its request and retires finished requests.
 // The workspace bytes of an iteration come from the same function that sizes the
 // workspace (ws_need_bytes), so admission and allocation agree.  Results are
@@ -68,17 +73,48 @@ static uint64_t slice_end(const Request &r, uint64_t per) {
     return per >= r.iv.hi - r.cursor ? r.iv.hi : r.cursor + per;
 }
 
-// Workspace bytes of an iteration in which each request runs its next `per` integers.
-static uint64_t iteration_bytes(bnx_ctx *c, const std::vector<std::shared_ptr<Request>> &rs, uint64_t per,
-                                std::vector<IvDev> &tmp) {
+// Workspace bytes of an iteration in which request i runs [cursor, ends[i]).
+static uint64_t iteration_bytes(bnx_ctx *c, const std::vector<std::shared_ptr<Request>> &rs,
+                                const std::vector<uint64_t> &ends, std::vector<IvDev> &tmp) {
     tmp.assign(rs.size(), IvDev{});
     for (size_t i = 0; i < rs.size(); i++) {
         tmp[i].lo = rs[i]->cursor;
-        tmp[i].hi = slice_end(*rs[i], per);
+        tmp[i].hi = ends[i];
     }
     PlanTotals t;
     plan_host(c, tmp.data(), rs.size(), &t);
     return ws_need_bytes(c, t, rs.size());
+}
+
+// ... in which each request runs its next `per` integers.
+static uint64_t iteration_bytes(bnx_ctx *c, const std::vector<std::shared_ptr<Request>> &rs, uint64_t per,
+                                std::vector<uint64_t> &ends, std::vector<IvDev> &tmp) {
+    ends.resize(rs.size());
+    for (size_t i = 0; i < rs.size(); i++) ends[i] = slice_end(*rs[i], per);
+    return iteration_bytes(c, rs, ends, tmp);
+}
+
+// Slice ends of an iteration: a request with at most `fin` integers left runs all of
+// them; every other request up to `base` integers; then up to `cap` integers in all, the
+// rest going to the requests in the order given (arrival).  Returns the integers of the
+// first two parts.
+static uint64_t cut_slices(const std::vector<std::shared_ptr<Request>> &rs, uint64_t fin, uint64_t base,
+                           uint64_t cap, std::vector<uint64_t> &ends) {
+    ends.resize(rs.size());
+    uint64_t used = 0;
+    for (size_t i = 0; i < rs.size(); i++) {
+        const uint64_t rem = rs[i]->iv.hi - rs[i]->cursor;
+        ends[i] = rem <= fin ? rs[i]->iv.hi : slice_end(*rs[i], base);
+        const uint64_t a = ends[i] - rs[i]->cursor;
+        used = a > UINT64_MAX - used ? UINT64_MAX : used + a;
+    }
+    uint64_t left = cap > used ? cap - used : 0;
+    for (size_t i = 0; i < rs.size() && left > 0; i++) {
+        const uint64_t more = std::min<uint64_t>(rs[i]->iv.hi - ends[i], left);
+        ends[i] += more;
+        left -= more;
+    }
+    return used;
 }
 
 static void publish_stats(bnx_ctx *c, const Server &S) {
@@ -89,6 +125,7 @@ static void publish_stats(bnx_ctx *c, const Server &S) {
 static void serve(bnx_ctx *c) {
     Server &S = *c->server;
     cudaSetDevice(c->device);
+    std::vector<uint64_t> ends;
     for (;;) {
         std::vector<std::shared_ptr<Request>> batch;
         {
@@ -98,7 +135,7 @@ static void serve(bnx_ctx *c) {
                 auto r = S.pending.front();
                 auto trial = S.active;
                 trial.push_back(r);
-                if (iteration_bytes(c, trial, S.cfg.slice, S.plan_tmp) > S.budget) {
+                if (iteration_bytes(c, trial, S.cfg.slice, ends, S.plan_tmp) > S.budget) {
                     if (S.active.empty()) {  // its first slice does not fit even alone: it never will
                         r->status = BNX_E_NOMEM;
                         r->done = true;
@@ -125,12 +162,36 @@ static void serve(bnx_ctx *c) {
             batch = S.active;
         }
         const size_t k = batch.size();
-        // this iteration's slice: an equal share of slice * max_active, at least `slice`,
-        // shortened while the iteration's workspace exceeds the budget
+        // this iteration's slices: as many integers in all as an equal share eq of
+        // slice * max_active (at least `slice` each) would give; a request with at most eq
+        // left finishes, every other one gets `slice`, and the rest go to those in arrival
+        // order.  While the workspace exceeds the budget, halve the total down to no extra
+        // share, then the per-request slice (and the finishing bound) down to one queue
+        // segment
         const uint64_t share = S.cfg.slice > UINT64_MAX / S.cfg.max_active ? UINT64_MAX : S.cfg.slice * S.cfg.max_active;
+        const uint64_t eq = std::max<uint64_t>(S.cfg.slice, share / k);
+        uint64_t cap = 0;
+        for (size_t i = 0; i < k; i++) {
+            const uint64_t a = slice_end(*batch[i], eq) - batch[i]->cursor;
+            cap = a > UINT64_MAX - cap ? UINT64_MAX : cap + a;
+        }
         const uint64_t seg = 1ull << c->seg_log2();
-        uint64_t per = std::max<uint64_t>(S.cfg.slice, share / k);
-        while (per > seg && iteration_bytes(c, batch, per, S.plan_tmp) > S.budget) per = std::max(seg, per / 2);
+        uint64_t base = S.cfg.slice, fin = eq;
+        for (;;) {
+            const uint64_t used = cut_slices(batch, fin, base, cap, ends);
+            if (iteration_bytes(c, batch, ends, S.plan_tmp) <= S.budget) break;
+            if (cap > used) {
+                cap = std::max(used, cap / 2);
+            } else if (fin > base) {
+                fin = base;
+                cap = 0;
+            } else if (base > seg) {
+                base = fin = std::max(seg, base / 2);
+                cap = 0;
+            } else {
+                break;  // one segment each still does not fit: the run reports BNX_E_NOMEM
+            }
+        }
         int rc = ensure_staging(c, k);
         if (rc == BNX_OK) {
             for (size_t i = 0; i < k; i++) {
@@ -138,7 +199,7 @@ static void serve(bnx_ctx *c) {
                 IvDev &d = c->h_ivs[i];
                 memset(&d, 0, sizeof d);
                 d.lo = r.cursor;
-                d.hi = slice_end(r, per);
+                d.hi = ends[i];
                 d.kinds = r.iv.kinds;
                 d.id = (uint32_t)i;
             }
@@ -162,7 +223,7 @@ static void serve(bnx_ctx *c) {
                     p.iv = r.iv.id;
                     r.pairs.push_back(p);
                 }
-                r.cursor = slice_end(r, per);
+                r.cursor = ends[i];
             } else {
                 r.status = rc;
                 r.cursor = r.iv.hi;
