@@ -51,6 +51,7 @@ extern "C" {
 #define BNX_E_BUSY 6       /* a served request is not finished yet */
 #define BNX_E_STATE 7      /* the call does not fit the context's state */
 #define BNX_E_OVERFLOW 8   /* a device-side capacity was exceeded */
+#define BNX_E_CANCELLED 9  /* a served request was cancelled before it finished */
 
 #define BNX_MAX_HI ((uint64_t)1 << 42)
 
@@ -166,6 +167,30 @@ int bnx_rad_segment(bnx_ctx *ctx, uint64_t lo, uint64_t len, uint64_t *rad_out, 
  * Errors: BNX_E_ARG, BNX_E_TRUNCATED, BNX_E_NOMEM, BNX_E_CUDA, BNX_E_OVERFLOW. */
 int bnx_search_segment(bnx_ctx *ctx, uint64_t lo, uint32_t len, uint32_t kinds, bnx_pair *out, size_t cap,
                        size_t *n_out);
+
+/* Checkpointed search: all pairs with lo <= n < hi of the given kinds, as
+ * bnx_search finds them, run as consecutive chunks of `chunk` integers.  After
+ * each chunk the progress -- the search (lo, hi, kinds), the next n to search
+ * and the pairs found so far -- is written to the file `path` (a new file
+ * renamed over the old one, so the file always holds a finished chunk).  A call
+ * that finds a checkpoint of the same search in `path` resumes after its last
+ * chunk; a checkpoint of another search gives BNX_E_STATE, an unreadable one
+ * BNX_E_ARG.  The paper's long search (Sec. 3.1) keeps only its chunk number;
+ * this keeps the pairs too, so a resumed search returns them all.
+ *  - max_chunks: at most that many chunks this call (BNX_CKPT_ALL: to hi; 0:
+ *    none, only the saved pairs are returned); a search not finished after them
+ *    returns BNX_E_BUSY (call again to go on), with the pairs so far in `out`.
+ *  - *next (may be NULL): the next n to search (hi once finished).
+ *  - out, cap, n_out: as bnx_search (HOST buffer, sorted by (n, m, kind)); on
+ *    BNX_E_TRUNCATED the progress is saved, and a call with max_chunks = 0 and a
+ *    larger buffer returns the pairs without searching.
+ * A finished search leaves its checkpoint (next = hi), so calling again returns
+ * the pairs without searching.  Blocking.  Errors: BNX_E_ARG, BNX_E_STATE,
+ * BNX_E_BUSY, BNX_E_TRUNCATED, BNX_E_NOMEM, BNX_E_CUDA, BNX_E_OVERFLOW. */
+#define BNX_CKPT_ALL UINT64_MAX
+int bnx_search_checkpointed(bnx_ctx *ctx, uint64_t lo, uint64_t hi, uint32_t kinds, const char *path,
+                            uint64_t chunk, uint64_t max_chunks, bnx_pair *out, size_t cap, size_t *n_out,
+                            uint64_t *next);
 
 /* Radicals of [lo, lo+len) without allocating any device memory -- for
  * callers that cannot call cudaMalloc (their device memory is owned by another
@@ -331,6 +356,7 @@ typedef struct {
                                 they finish at once with BNX_E_NOMEM */
     uint64_t budget_bytes;   /* the loop's workspace budget */
     uint64_t ws_peak_bytes;  /* largest workspace held after an iteration (<= budget_bytes) */
+    uint64_t cancelled;      /* requests cancelled before they finished */
 } bnx_server_stats;
 
 /* Start the serving loop on a background host thread.  Each iteration
@@ -358,6 +384,14 @@ int bnx_workspace_bytes(bnx_ctx *ctx, const bnx_interval *iv, size_t k, uint64_t
 
 /* Queue a request; *ticket identifies it.  Never blocks on the device. */
 int bnx_server_submit(bnx_ctx *ctx, const bnx_interval *iv, uint64_t *ticket);
+
+/* Cancel a request.  One still waiting for a slot is dropped at once; one on the
+ * device finishes the slice it is running and is retired at the end of that
+ * iteration, its pairs discarded.  Either way it counts as completed and
+ * cancelled, and bnx_server_poll then returns BNX_E_CANCELLED (and releases the
+ * ticket).  A request that already finished is left as it is.  Never blocks on
+ * the device.  Errors: BNX_E_ARG (unknown ticket), BNX_E_STATE (not serving). */
+int bnx_server_cancel(bnx_ctx *ctx, uint64_t ticket);
 
 /* BNX_E_BUSY while the request runs; BNX_OK once done, with its pairs copied to
  * the host buffer `out` (sorted by (n, m, kind)) and latency_s = completion time

@@ -13,7 +13,8 @@ import threading
 from . import build as _build
 
 BNX_OK, BNX_E_ARG, BNX_E_TRUNCATED, BNX_E_NOMEM, BNX_E_CUDA = 0, 1, 2, 3, 4
-BNX_E_TIMEOUT, BNX_E_BUSY, BNX_E_STATE, BNX_E_OVERFLOW = 5, 6, 7, 8
+BNX_E_TIMEOUT, BNX_E_BUSY, BNX_E_STATE, BNX_E_OVERFLOW, BNX_E_CANCELLED = 5, 6, 7, 8, 9
+BNX_CKPT_ALL = (1 << 64) - 1
 BNX_MAX_HI = 1 << 42
 
 u64, u32, i32, sz, vp = ctypes.c_uint64, ctypes.c_uint32, ctypes.c_int, ctypes.c_size_t, ctypes.c_void_p
@@ -52,7 +53,7 @@ class bnx_server_cfg(ctypes.Structure):
 
 class bnx_server_stats(ctypes.Structure):
     _fields_ = [("submitted", u64), ("completed", u64), ("iterations", u64), ("deferred", u64),
-                ("rejected", u64), ("budget_bytes", u64), ("ws_peak_bytes", u64)]
+                ("rejected", u64), ("budget_bytes", u64), ("ws_peak_bytes", u64), ("cancelled", u64)]
 
     def as_dict(self):
         return {f: int(getattr(self, f)) for f, _ in self._fields_}
@@ -104,6 +105,9 @@ def lib(auto_build: bool = True):
             "bnx_arm_lookback_timeout": ([vp, u32], i32),
             "bnx_server_start": ([vp, P(bnx_server_cfg)], i32),
             "bnx_server_submit": ([vp, P(bnx_interval), P(u64)], i32),
+            "bnx_server_cancel": ([vp, u64], i32),
+            "bnx_search_checkpointed": ([vp, u64, u64, u32, ctypes.c_char_p, u64, u64, P(bnx_pair), sz, P(sz),
+                                         P(u64)], i32),
             "bnx_server_poll": ([vp, u64, P(bnx_pair), sz, P(sz), P(ctypes.c_double)], i32),
             "bnx_server_stop": ([vp], i32),
             "bnx_server_get_stats": ([vp, P(bnx_server_stats)], i32),
@@ -332,6 +336,29 @@ def bnx_server_poll(ctx, ticket: int):
         return _pairs(buf, int(n.value)), float(lat.value)
 
 
+def bnx_server_cancel(ctx, ticket: int) -> None:
+    _check(lib().bnx_server_cancel(ctx, ticket))
+
+
+def bnx_search_checkpointed(ctx, lo: int, hi: int, kinds: int, path: str, chunk: int, max_chunks: int = BNX_CKPT_ALL):
+    """(pairs so far, next n to search, finished).  Runs at most max_chunks chunks of
+    `chunk` integers, saving the progress to `path` after each; resumes from `path`."""
+    p = os.fsencode(path)
+    nxt = u64()
+    cap = 256
+    while True:
+        buf = (bnx_pair * cap)()
+        n = sz()
+        rc = lib().bnx_search_checkpointed(ctx, lo, hi, kinds, p, chunk, max_chunks, buf, cap, ctypes.byref(n),
+                                           ctypes.byref(nxt))
+        if rc == BNX_E_TRUNCATED:  # the progress is saved: read the pairs back without searching
+            cap, max_chunks = int(n.value) + 16, 0
+            continue
+        if rc not in (BNX_OK, BNX_E_BUSY):
+            _check(rc)
+        return _pairs(buf, int(n.value)), int(nxt.value), rc == BNX_OK
+
+
 def bnx_server_stop(ctx) -> None:
     _check(lib().bnx_server_stop(ctx))
 
@@ -383,6 +410,9 @@ class Context:
 
     def search(self, lo, hi, kinds=3):
         return bnx_search(self.h, lo, hi, kinds)
+
+    def search_checkpointed(self, lo, hi, kinds, path, chunk, max_chunks=BNX_CKPT_ALL):
+        return bnx_search_checkpointed(self.h, lo, hi, kinds, path, chunk, max_chunks)
 
     def search_segment(self, lo, length, kinds=3):
         return bnx_search_segment(self.h, lo, length, kinds)

@@ -2,6 +2,8 @@
 // (captured once as a CUDA graph and replayed), and the C ABI entry points
 // declared in include/benelux.h.
 #include <algorithm>
+#include <unistd.h>
+#include <cerrno>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -629,6 +631,7 @@ const char *bnx_strerror(int code) {
         case BNX_E_BUSY: return "busy";
         case BNX_E_STATE: return "invalid state";
         case BNX_E_OVERFLOW: return "device capacity exceeded";
+        case BNX_E_CANCELLED: return "cancelled";
         default: return "unknown error";
     }
 }
@@ -944,6 +947,101 @@ int bnx_search_segment(bnx_ctx *c, uint64_t lo, uint32_t len, uint32_t kinds, bn
     if (len < 1 || lo < 1 || len > c->max_hi || lo > c->max_hi - len)
         return fail(BNX_E_ARG, "need len >= 1, lo >= 1 and lo + len <= max_hi");
     return search_one(c, lo, lo + len, kinds, out, cap, n_out);
+}
+
+// Checkpoint file of bnx_search_checkpointed: this header, then `npairs` bnx_pair
+// records (host byte order).
+struct CkptHeader {
+    char magic[8];  // "BNXCKPT1"
+    uint64_t lo, hi;
+    uint32_t kinds, pad;
+    uint64_t next, npairs;
+};
+static const char kCkptMagic[8] = {'B', 'N', 'X', 'C', 'K', 'P', 'T', '1'};
+
+// BNX_OK with *found = false when the file does not exist
+static int read_checkpoint(const char *path, CkptHeader *h, std::vector<bnx_pair> &pairs, bool *found) {
+    *found = false;
+    FILE *f = fopen(path, "rb");
+    if (!f) {
+        if (errno == ENOENT) return BNX_OK;
+        return fail(BNX_E_ARG, "cannot open checkpoint %s", path);
+    }
+    int rc = BNX_OK;
+    if (fread(h, sizeof *h, 1, f) != 1 || memcmp(h->magic, kCkptMagic, 8) != 0 || h->next < h->lo ||
+        h->next > h->hi || h->npairs > ((uint64_t)1 << 40)) {
+        rc = fail(BNX_E_ARG, "%s is not a checkpoint of this library", path);
+    } else {
+        pairs.resize(h->npairs);
+        if (h->npairs && fread(pairs.data(), sizeof(bnx_pair), h->npairs, f) != h->npairs)
+            rc = fail(BNX_E_ARG, "checkpoint %s is truncated", path);
+        else if (fgetc(f) != EOF)
+            rc = fail(BNX_E_ARG, "checkpoint %s has trailing bytes", path);
+    }
+    fclose(f);
+    if (rc == BNX_OK) *found = true;
+    return rc;
+}
+
+// write to path.tmp, flush it to the disk, then rename it over path
+static int write_checkpoint(const char *path, const CkptHeader &h, const std::vector<bnx_pair> &pairs) {
+    const std::string tmp = std::string(path) + ".tmp";
+    FILE *f = fopen(tmp.c_str(), "wb");
+    if (!f) return fail(BNX_E_ARG, "cannot write checkpoint %s", tmp.c_str());
+    bool ok = fwrite(&h, sizeof h, 1, f) == 1;
+    if (ok && !pairs.empty()) ok = fwrite(pairs.data(), sizeof(bnx_pair), pairs.size(), f) == pairs.size();
+    ok = ok && fflush(f) == 0 && fsync(fileno(f)) == 0;
+    ok = (fclose(f) == 0) && ok;
+    if (!ok || rename(tmp.c_str(), path) != 0) {
+        remove(tmp.c_str());
+        return fail(BNX_E_ARG, "cannot write checkpoint %s", path);
+    }
+    return BNX_OK;
+}
+
+int bnx_search_checkpointed(bnx_ctx *c, uint64_t lo, uint64_t hi, uint32_t kinds, const char *path, uint64_t chunk,
+                            uint64_t max_chunks, bnx_pair *out, size_t cap, size_t *n_out, uint64_t *next) {
+    if (!c || !path) return fail(BNX_E_ARG, "NULL argument");
+    if (chunk < 1) return fail(BNX_E_ARG, "chunk must be >= 1");
+    int rc = validate_interval(c, lo, hi, kinds);
+    if (rc) return rc;
+    CkptHeader h;
+    std::vector<bnx_pair> pairs;
+    bool found = false;
+    if ((rc = read_checkpoint(path, &h, pairs, &found))) return rc;
+    if (found && (h.lo != lo || h.hi != hi || h.kinds != kinds))
+        return fail(BNX_E_STATE, "%s holds another search: [%llu, %llu) kinds %u", path, (unsigned long long)h.lo,
+                    (unsigned long long)h.hi, h.kinds);
+    if (!found) {
+        memset(&h, 0, sizeof h);
+        memcpy(h.magic, kCkptMagic, 8);
+        h.lo = lo;
+        h.hi = hi;
+        h.kinds = kinds;
+        h.next = lo;
+    }
+    std::vector<bnx_pair> part(64);
+    for (uint64_t done = 0; h.next < hi && done < max_chunks; done++) {
+        const uint64_t end = chunk >= hi - h.next ? hi : h.next + chunk;
+        size_t np = 0;
+        rc = search_one(c, h.next, end, kinds, part.data(), part.size(), &np);
+        if (rc == BNX_E_TRUNCATED) {
+            part.resize(np);
+            rc = search_one(c, h.next, end, kinds, part.data(), part.size(), &np);
+        }
+        if (rc) return rc;  // the checkpoint still holds the last finished chunk
+        pairs.insert(pairs.end(), part.begin(), part.begin() + np);
+        h.next = end;
+        h.npairs = pairs.size();
+        if ((rc = write_checkpoint(path, h, pairs))) return rc;
+    }
+    if (next) *next = h.next;
+    if (n_out) *n_out = pairs.size();
+    if (pairs.size() > cap) return fail(BNX_E_TRUNCATED, "%zu pairs, buffer holds %zu", pairs.size(), cap);
+    if (!pairs.empty() && !out) return fail(BNX_E_ARG, "out is NULL");
+    if (!pairs.empty()) memcpy(out, pairs.data(), pairs.size() * sizeof(bnx_pair));
+    if (h.next < hi) return fail(BNX_E_BUSY, "stopped at %llu: call again to resume", (unsigned long long)h.next);
+    return BNX_OK;
 }
 
 int bnx_batch(bnx_ctx *c, const bnx_interval *ivs, size_t k, bnx_pair *out, size_t cap, size_t *n_out,

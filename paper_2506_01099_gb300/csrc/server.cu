@@ -19,7 +19,8 @@
 //      then the per-request `slice` (down to one queue segment); the workspace is
 //      sized under the same budget, so the budget bounds the device memory the loop
 //      holds;
-//   3. appends each slice's pairs to its request and retires finished requests.
+//   3. appends each slice's pairs to its request and retires finished requests
+//      (and cancelled ones, whose pairs are discarded).
 // The workspace bytes of an iteration come from the same function that sizes the
 // workspace (ws_need_bytes), so admission and allocation agree.  Results are
 // exact, so a request's pairs are the same alone and in any mix.
@@ -48,6 +49,7 @@ struct Request {
     Clock::time_point t_submit, t_done;
     bool done = false;
     bool deferred = false;  // waited for memory at least once
+    bool cancelled = false;  // bnx_server_cancel: retire at the end of the current iteration
     int status = BNX_OK;
 };
 
@@ -154,6 +156,21 @@ static void serve(bnx_ctx *c) {
                 S.active.push_back(r);
                 S.pending.pop_front();
             }
+            {  // requests cancelled while waiting between iterations
+                std::vector<std::shared_ptr<Request>> keep;
+                for (auto &r : S.active) {
+                    if (r->cancelled) {
+                        r->status = BNX_E_CANCELLED;
+                        r->done = true;
+                        r->t_done = Clock::now();
+                        S.st.completed++;
+                        S.st.cancelled++;
+                    } else {
+                        keep.push_back(r);
+                    }
+                }
+                S.active.swap(keep);
+            }
             publish_stats(c, S);
             if (S.active.empty()) {
                 S.cv.wait_for(lk, std::chrono::milliseconds(50));
@@ -217,6 +234,14 @@ static void serve(bnx_ctx *c) {
         std::vector<std::shared_ptr<Request>> still;
         for (size_t i = 0; i < k; i++) {
             Request &r = *batch[i];
+            if (r.cancelled) {  // cancelled during this iteration: its slice's pairs are dropped
+                r.status = BNX_E_CANCELLED;
+                r.done = true;
+                r.t_done = Clock::now();
+                S.st.completed++;
+                S.st.cancelled++;
+                continue;
+            }
             if (rc == BNX_OK) {
                 for (uint64_t e = S.offs[i]; e < S.offs[i + 1]; e++) {
                     bnx_pair p = S.buf[e];
@@ -299,6 +324,31 @@ int bnx_server_submit(bnx_ctx *c, const bnx_interval *iv, uint64_t *ticket) {
     }
     S.cv.notify_one();
     *ticket = r->ticket;
+    return BNX_OK;
+}
+
+int bnx_server_cancel(bnx_ctx *c, uint64_t ticket) {
+    if (!c) return fail(BNX_E_ARG, "NULL context");
+    if (!c->serving.load() || !c->server) return fail(BNX_E_STATE, "not serving");
+    Server &S = *c->server;
+    std::lock_guard<std::mutex> lk(S.m);
+    auto it = S.all.find(ticket);
+    if (it == S.all.end()) return fail(BNX_E_ARG, "unknown ticket %llu", (unsigned long long)ticket);
+    Request &r = *it->second;
+    if (r.done || r.cancelled) return BNX_OK;
+    r.cancelled = true;
+    for (auto p = S.pending.begin(); p != S.pending.end(); ++p) {
+        if (p->get() == &r) {  // not admitted yet: drop it now
+            S.pending.erase(p);
+            r.status = BNX_E_CANCELLED;
+            r.done = true;
+            r.t_done = Clock::now();
+            S.st.completed++;
+            S.st.cancelled++;
+            publish_stats(c, S);
+            break;
+        }
+    }
     return BNX_OK;
 }
 

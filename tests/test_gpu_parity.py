@@ -553,6 +553,75 @@ def test_server_admission_by_memory(B, orc):
     assert alone[0] == [(1048577, 1099513724928, 2)]
 
 
+def test_search_checkpointed_resumes(B, ctx, orc, tmp_path):
+    """A long search run in chunks stops after a few (its progress in the checkpoint
+    file), is read back without searching, resumes in a new context (as after a restart)
+    and ends with exactly the pairs of one uninterrupted search; the file refuses another
+    search and a corrupt file is refused."""
+    lo, hi = 2**40 - 2**22, 2**40 + 2**22 + 12345  # both kinds' family members near 2^40
+    want = theorem1_pairs(lo, hi)
+    assert len(want) == 2 and want == orc.pairs_crt(lo, hi)
+    path, chunk = str(tmp_path / "search.ckpt"), 1 << 20
+    got, nxt, fin = ctx.search_checkpointed(lo, hi, 3, path, chunk, max_chunks=3)
+    assert not fin and nxt == lo + 3 * chunk and got == [p for p in want if p[1] < nxt]
+    assert ctx.search_checkpointed(lo, hi, 3, path, chunk, max_chunks=0) == (got, nxt, False)
+    with B.Context(0, max_hi=MAX_HI) as c2:
+        got2, nxt2, fin2 = c2.search_checkpointed(lo, hi, 3, path, chunk)
+    assert fin2 and nxt2 == hi and got2 == want == ctx.search(lo, hi)
+    assert ctx.search_checkpointed(lo, hi, 3, path, chunk) == (want, hi, True)  # finished: no search
+    with pytest.raises(B.BnxError) as e:
+        ctx.search_checkpointed(lo, hi + 1, 3, path, chunk)
+    assert e.value.code == B.BNX_E_STATE
+    with open(path, "r+b") as f:  # a corrupt header
+        f.write(b"NOTACKPT")
+    with pytest.raises(B.BnxError) as e:
+        ctx.search_checkpointed(lo, hi, 3, path, chunk)
+    assert e.value.code == B.BNX_E_ARG
+
+
+def test_server_cancel(B):
+    """A waiting request cancelled is dropped at once, an active one is retired at the end
+    of its iteration; both poll as BNX_E_CANCELLED, the counters record them, and the
+    request behind them still gets exactly its pairs."""
+    import time
+
+    with B.Context(0, max_hi=MAX_HI) as c:
+        B.bnx_server_start(c.h, max_active=1, slice_len=1 << 26)  # one slot: the others wait
+        try:
+            big = B.bnx_server_submit(c.h, 2**40, 2**40 + 2**38)  # about four thousand iterations
+            small = B.bnx_server_submit(c.h, 1, 1 << 20)
+            lo, hi = 2**40 - 2**22, 2**40 + 2**22
+            last = B.bnx_server_submit(c.h, lo, hi)
+            B.bnx_server_cancel(c.h, small)
+            time.sleep(0.05)
+            assert B.bnx_server_poll(c.h, big) is None  # still running
+            B.bnx_server_cancel(c.h, big)
+            B.bnx_server_cancel(c.h, big)  # a second cancel changes nothing
+            with pytest.raises(B.BnxError) as e:
+                B.bnx_server_cancel(c.h, 10**9)
+            assert e.value.code == B.BNX_E_ARG
+            codes = {}
+            got = None
+            t0 = time.time()
+            while (len(codes) < 2 or got is None) and time.time() - t0 < 120:
+                for t in (big, small):
+                    if t not in codes:
+                        try:
+                            if B.bnx_server_poll(c.h, t) is not None:
+                                codes[t] = B.BNX_OK
+                        except B.BnxError as err:
+                            codes[t] = err.code
+                if got is None:
+                    got = B.bnx_server_poll(c.h, last)
+                time.sleep(0.002)
+            st = B.bnx_server_get_stats(c.h)
+        finally:
+            B.bnx_server_stop(c.h)
+    assert codes == {big: B.BNX_E_CANCELLED, small: B.BNX_E_CANCELLED}
+    assert got is not None and got[0] == theorem1_pairs(lo, hi)
+    assert st["cancelled"] == 2 and st["completed"] == 3 and st["submitted"] == 3, st
+
+
 def test_server_rejects_a_request_that_never_fits(B):
     """A budget below one slice's workspace: the request finishes at once with BNX_E_NOMEM."""
     import time
