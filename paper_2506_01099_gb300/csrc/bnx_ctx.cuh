@@ -6,10 +6,23 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "benelux.h"
 #include "bnx_internal.cuh"
 
 namespace bnx {
+
+// An NVTX range over a host stage (planning, workspace, the pipeline run, copies, a
+// serving iteration, a checkpoint): visible in a timeline profiler, and next to free
+// when none is attached (NVTX v3 binds to a tool only when one is loaded).
+struct NvtxRange {
+    explicit NvtxRange(const char *name) { nvtxRangePushA(name); }
+    ~NvtxRange() { nvtxRangePop(); }
+    NvtxRange(const NvtxRange &) = delete;
+    NvtxRange &operator=(const NvtxRange &) = delete;
+};
+
 
 struct DevBuf {
     void *p = nullptr;

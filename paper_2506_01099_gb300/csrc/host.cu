@@ -586,18 +586,30 @@ int validate_interval(const bnx_ctx *c, uint64_t lo, uint64_t hi, uint32_t kinds
 // overflow; copies the sorted pairs (and per-interval offsets) to the host.
 int search_staged(bnx_ctx *c, size_t k, bnx_pair *out, size_t cap, size_t *n_out, uint64_t *offsets,
                   uint64_t budget) {
+    NvtxRange r_all("bnx.search");
     PlanTotals t;
-    plan_host(c, c->h_ivs, k, &t);
+    {
+        NvtxRange r("bnx.plan");
+        plan_host(c, c->h_ivs, k, &t);
+    }
     for (int attempt = 0; attempt < 4; attempt++) {
-        int rc = ensure_ws(c, t, k, budget);
+        int rc;
+        {
+            NvtxRange r("bnx.workspace");
+            rc = ensure_ws(c, t, k, budget);
+        }
         if (rc) return rc;
-        rc = run_search(c, k, true);
+        {
+            NvtxRange r("bnx.pipeline");  // graph launch (or capture) and the wait for it
+            rc = run_search(c, k, true);
+        }
         if (rc) return rc;
         bool rerun = false;
         rc = check_counters(c, &rerun);
         if (rerun) continue;
         if (rc) return rc;
         fill_stats(c, t.integers);
+        NvtxRange r_out("bnx.copy_out");
         const size_t np = (size_t)c->h_ctr->n_pairs;
         if (n_out) *n_out = np;
         const size_t ncopy = std::min(np, cap);
@@ -1023,6 +1035,7 @@ int bnx_search_checkpointed(bnx_ctx *c, uint64_t lo, uint64_t hi, uint32_t kinds
     std::vector<bnx_pair> part(64);
     for (uint64_t done = 0; h.next < hi && done < max_chunks; done++) {
         const uint64_t end = chunk >= hi - h.next ? hi : h.next + chunk;
+        NvtxRange r_chunk("bnx.checkpoint.chunk");
         size_t np = 0;
         rc = search_one(c, h.next, end, kinds, part.data(), part.size(), &np);
         if (rc == BNX_E_TRUNCATED) {
@@ -1033,6 +1046,7 @@ int bnx_search_checkpointed(bnx_ctx *c, uint64_t lo, uint64_t hi, uint32_t kinds
         pairs.insert(pairs.end(), part.begin(), part.begin() + np);
         h.next = end;
         h.npairs = pairs.size();
+        NvtxRange r_write("bnx.checkpoint.write");
         if ((rc = write_checkpoint(path, h, pairs))) return rc;
     }
     if (next) *next = h.next;

@@ -179,6 +179,7 @@ static void serve(bnx_ctx *c) {
             batch = S.active;
         }
         const size_t k = batch.size();
+        NvtxRange r_it("bnx.serve.iteration");
         // this iteration's slices: as many integers in all as an equal share eq of
         // slice * max_active (at least `slice` each) would give; a request with at most eq
         // left finishes, every other one gets `slice`, and the rest go to those in arrival
