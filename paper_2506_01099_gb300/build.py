@@ -18,6 +18,10 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(PKG, "_build")
 LIB = os.path.join(BUILD, "libbenelux.so")
+# the bounds-checked library: tile and bucket indices checked in the kernels (BNX_GUARD),
+# an index outside its buffer skips the access and fails the run with an error
+CHECKED_BUILD = os.path.join(BUILD, "checked")
+CHECKED_LIB = os.path.join(CHECKED_BUILD, "libbenelux.so")
 SOURCES = ["tables.cu", "sieve.cu", "sieve_log.cu", "rad.cu", "verify.cu", "host.cu", "server.cu", "noalloc.cu",
            "alg3.cu", "alg2.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -39,25 +43,31 @@ def _deps() -> list[str]:
     return files + [os.path.abspath(__file__)]
 
 
-def up_to_date() -> bool:
-    if not os.path.exists(LIB):
+def up_to_date(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return False
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
-def build(verbose: bool = False, force: bool = False, extra: list[str] | None = None) -> str:
-    if not force and up_to_date():
-        return LIB
+def build_checked(verbose: bool = False, force: bool = False) -> str:
+    """The bounds-checked library (-DBNX_CHECK_BOUNDS) in _build/checked/."""
+    return build(verbose, force, ["-DBNX_CHECK_BOUNDS"], out_dir=CHECKED_BUILD)
+
+
+def build(verbose: bool = False, force: bool = False, extra: list[str] | None = None, out_dir: str = BUILD) -> str:
+    lib_path = os.path.join(out_dir, "libbenelux.so")
+    if not force and up_to_date(lib_path):
+        return lib_path
     nvcc = _nvcc()
-    os.makedirs(BUILD, exist_ok=True)
+    os.makedirs(out_dir, exist_ok=True)
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-I", INCLUDE, "-I", CSRC,
                     "--expt-relaxed-constexpr"] + (extra or [])
     if verbose:
         flags += ["-Xptxas", "-v"]
 
     def one(src):
-        obj = os.path.join(BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(out_dir, src.replace(".cu", ".o"))
         cmd = [nvcc] + flags + ["-c", os.path.join(CSRC, src), "-o", obj]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -69,15 +79,15 @@ def build(verbose: bool = False, force: bool = False, extra: list[str] | None = 
     if verbose:
         for _, log in results:
             sys.stderr.write(log)
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     cuda_lib = os.path.join(_cuda_home(nvcc), "lib64")
     cmd = [nvcc] + ARCH + ["-shared", "-cudart", "shared", "-o", tmp] + [o for o, _ in results] + [
         "-Xlinker", f"-rpath,{cuda_lib}", "-lpthread"]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 if __name__ == "__main__":

@@ -179,6 +179,22 @@ constexpr unsigned kErrBucketOverflow = 4u;
 constexpr unsigned kErrHashFull = 8u;
 constexpr unsigned kErrSchedule = 32u;  // a strike schedule did not fit its array (never expected)
 constexpr unsigned kErrCandOverflow = 64u;
+constexpr unsigned kErrBounds = 256u;  // bounds-checked build: an index fell outside its buffer
+
+// Bounds checks of the tile and bucket indices.  Built with -DBNX_CHECK_BOUNDS (the
+// checked library of build.py), BNX_GUARD(cond, err) is cond, and a false cond sets
+// kErrBounds in *err: the access it guards is skipped and the run fails with an error,
+// nothing traps.  In the normal build it is true, and the guarded access runs
+// unconditionally.
+#ifdef BNX_CHECK_BOUNDS
+__device__ __forceinline__ bool bnx_guard(bool ok, unsigned int *err) {
+    if (!ok) atomicOr(err, kErrBounds);
+    return ok;
+}
+#define BNX_GUARD(cond, err) bnx_guard((cond), (err))
+#else
+#define BNX_GUARD(cond, err) true
+#endif
 
 // Everything a pipeline's kernels read.  Passed by value to every launch; the
 // sizes that vary per run live in device memory (Counters, IvDev) so that one

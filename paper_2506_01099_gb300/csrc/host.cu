@@ -550,6 +550,7 @@ int check_counters(bnx_ctx *c, bool *rerun) {
         *rerun = true;
         return BNX_E_OVERFLOW;
     }
+    if (h.err & kErrBounds) return fail(BNX_E_OVERFLOW, "a device index fell outside its buffer (flags 0x%x)", h.err);
     if (h.err) return fail(BNX_E_OVERFLOW, "device capacity exceeded (flags 0x%x)", h.err);
     return BNX_OK;
 }
@@ -799,10 +800,17 @@ int bnx_rad_segment(bnx_ctx *c, uint64_t lo, uint64_t len, uint64_t *rad_out, ui
     if (rc == BNX_OK) {
         cudaError_t e = cudaMemcpyAsync(rad_out, d_rad, bytes, cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess && sq_out) e = cudaMemcpyAsync(sq_out, d_sq, bytes, cudaMemcpyDeviceToHost, s);
+        // the run's error flags (a blocking call can report them)
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(&c->h_ctr->err, &static_cast<Counters *>(c->ctr.p)->err, sizeof(c->h_ctr->err),
+                                cudaMemcpyDeviceToHost, s);
         if (e == cudaSuccess) e = cudaStreamSynchronize(s);
         if (e != cudaSuccess) {
             cudaGetLastError();
             rc = fail(BNX_E_CUDA, "copy of the radicals to the host: %s", cudaGetErrorString(e));
+        } else if (c->h_ctr->err) {
+            rc = fail(BNX_E_OVERFLOW, "the radical run flagged 0x%x (0x%x: an index outside its buffer)",
+                      c->h_ctr->err, kErrBounds);
         }
     }
     if (c->rad_stage.bytes > ((size_t)1 << 28)) {  // a large staging buffer is not kept

@@ -79,6 +79,9 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_rad(Plan P) {
     const uint32_t nspp = P.n_spp;
     const RadLayout lay = rad_layout(tile_log2, nspp, P.n_sched);
     uint32_t *tile = reinterpret_cast<uint32_t *>(smem_raw + lay.tile);
+    // words of the tile region and the error word, for the bounds-checked build (BNX_GUARD)
+    const uint32_t tile_words = (uint32_t)((lay.spp - lay.tile) / sizeof(uint32_t));
+    unsigned int *const gerr = &P.ctr->err;
     uint32_t *sq = reinterpret_cast<uint32_t *>(smem_raw + lay.spp);
     uint32_t *sp = sq + nspp;
     uint32_t *soff = sp + nspp;   // first multiple of q in the current tile
@@ -166,7 +169,8 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_rad(Plan P) {
             const uint32_t r = (uint32_t)(seg_lo % q);
             soff[j] = r ? q - r : 0;
         }
-        for (uint32_t e = tid; e < nbc; e += NT) bcache[e] = P.bent[b0 + e];
+        for (uint32_t e = tid; e < nbc; e += NT)
+            if (BNX_GUARD(b0 + e < P.bucket_cap && e < (uint32_t)kRadBucketCache, gerr)) bcache[e] = P.bent[b0 + e];
         const uint32_t nsched = s_nsched;
 
         for (uint32_t t0 = 0; t0 < seg_len; t0 += LT) {
@@ -192,16 +196,17 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_rad(Plan P) {
                 const uint32_t e = sched[g];
                 const uint32_t j = e & 255u;
                 const uint32_t x = soff[j] + (((e >> 8) << 5) + lane) * sq[j];
-                if (x <= tl) strike32(tile, x, sp[j]);
+                if (x <= tl && BNX_GUARD(x < tile_words, gerr)) strike32(tile, x, sp[j]);
             }
             // large prime powers: this segment's bucket
             for (uint32_t e = tid; e < nbc; e += NT) {
                 const uint2 h = bcache[e];
-                if (h.x >= t0 && h.x <= t0 + tl) strike32(tile, h.x - t0, h.y);
+                if (h.x >= t0 && h.x <= t0 + tl && BNX_GUARD(h.x - t0 < tile_words, gerr)) strike32(tile, h.x - t0, h.y);
             }
             for (unsigned long long e = b0 + kRadBucketCache + tid; e < b1; e += NT) {
+                if (!BNX_GUARD(e < P.bucket_cap, gerr)) break;
                 const uint2 h = P.bent[e];
-                if (h.x >= t0 && h.x <= t0 + tl) strike32(tile, h.x - t0, h.y);
+                if (h.x >= t0 && h.x <= t0 + tl && BNX_GUARD(h.x - t0 < tile_words, gerr)) strike32(tile, h.x - t0, h.y);
             }
             __syncthreads();
             // offsets of the next tile: (off - L_tile) mod q
@@ -215,7 +220,8 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_rad(Plan P) {
                 const uint32_t tz = (uint32_t)(__ffsll((long long)x) - 1);
                 const uint64_t xo = x >> tz;
                 uint64_t so = s32;
-                if (so == 0) so = sodd_exact(x, t0 + i, &sprimes, P.sqrt_q, P.bent, b0, b1);  // past 2^32
+                if (so == 0 && BNX_GUARD(b1 <= P.bucket_cap, gerr))
+                    so = sodd_exact(x, t0 + i, &sprimes, P.sqrt_q, P.bent, b0, b1);  // past 2^32
                 uint64_t inv;
                 if (so < 256) inv = s_inv[so >> 1];
                 else inv = inv64(so);
@@ -232,6 +238,7 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_rad(Plan P) {
             const uint32_t tv = vec ? (uint32_t)min((uint64_t)tl, P.rad_len - g0) & ~1u : 0u;
             for (uint32_t i = 2 * tid; i < tv; i += 2 * NT) {
                 uint64_t r0, q0, r1, q1;
+                if (!BNX_GUARD(i + 1 < tile_words, gerr)) continue;
                 const uint2 s2 = *reinterpret_cast<const uint2 *>(tile + i);  // i even: 8-byte aligned
                 finish(i, s2.x, &r0, &q0);
                 finish(i + 1, s2.y, &r1, &q1);
@@ -242,7 +249,8 @@ __global__ void __launch_bounds__(NT, NT <= 256 ? 3 : 1) k_rad(Plan P) {
                 const uint64_t gi = t_lo + i - P.rad_lo;
                 if (gi < P.rad_len) {
                     uint64_t r, q;
-                    finish(i, tile[i], &r, &q);
+                    if (BNX_GUARD(i < tile_words, gerr)) finish(i, tile[i], &r, &q);
+                    else r = q = 0;
                     P.rad_out[gi] = r;
                     if (P.sq_out) P.sq_out[gi] = q;
                 }

@@ -125,31 +125,38 @@ __device__ __forceinline__ void bucket_hit(const Plan &P, const IvDev &iv, uint6
     const uint64_t d = y - iv.lo;
     const uint64_t s = d >> P.seg_log2;
     const uint32_t o = (uint32_t)(d & (lseg - 1));
+    // (bounds-checked build: every entry lands inside its segment's range of the array)
+    unsigned int *const gerr = &P.ctr->err;
     if (FILL && gcur) {
         if (s < nseg) {
             const uint64_t seg = iv.seg_base + s;
-            P.bent[P.boff[seg] + atomicAdd(&P.bcnt[seg], 1u)] = make_uint2(o, p);
+            const unsigned long long at = P.boff[seg] + atomicAdd(&P.bcnt[seg], 1u);
+            if (BNX_GUARD(at < P.boff[seg + 1] && at < P.bucket_cap, gerr)) P.bent[at] = make_uint2(o, p);
         }
         if (o == 0 && s > 0) {  // the previous segment's halo value
             const uint64_t seg = iv.seg_base + s - 1;
-            P.bent[P.boff[seg] + atomicAdd(&P.bcnt[seg], 1u)] = make_uint2((uint32_t)lseg, p);
+            const unsigned long long at = P.boff[seg] + atomicAdd(&P.bcnt[seg], 1u);
+            if (BNX_GUARD(at < P.boff[seg + 1] && at < P.bucket_cap, gerr)) P.bent[at] = make_uint2((uint32_t)lseg, p);
         }
         return;
     }
     if (s < nseg) {
         const uint32_t l = (uint32_t)(s - s_first);
         const uint32_t pos = atomicAdd(&hist[l], 1u);
-        if (FILL) P.bent[sbase[l] + pos] = make_uint2(o, p);
+        if (FILL && BNX_GUARD(sbase[l] + pos < P.boff[iv.seg_base + s + 1] && sbase[l] + pos < P.bucket_cap, gerr))
+            P.bent[sbase[l] + pos] = make_uint2(o, p);
     }
     if (o == 0 && s > 0) {
         if (s > s_first) {  // halo of a segment of this chunk
             const uint32_t l = (uint32_t)(s - 1 - s_first);
             const uint32_t pos = atomicAdd(&hist[l], 1u);
-            if (FILL) P.bent[sbase[l] + pos] = make_uint2((uint32_t)lseg, p);
+            if (FILL && BNX_GUARD(sbase[l] + pos < P.boff[iv.seg_base + s] && sbase[l] + pos < P.bucket_cap, gerr))
+                P.bent[sbase[l] + pos] = make_uint2((uint32_t)lseg, p);
         } else {  // halo of the previous chunk's last segment: written from its end
             const uint64_t seg = iv.seg_base + s - 1;
             const uint32_t pos = atomicAdd(&P.bcnt[seg], 1u);
-            if (FILL) P.bent[P.boff[seg + 1] - 1 - pos] = make_uint2((uint32_t)lseg, p);
+            if (FILL && BNX_GUARD(pos < P.boff[seg + 1] - P.boff[seg] && P.boff[seg + 1] <= P.bucket_cap, gerr))
+                P.bent[P.boff[seg + 1] - 1 - pos] = make_uint2((uint32_t)lseg, p);
         }
     }
 }

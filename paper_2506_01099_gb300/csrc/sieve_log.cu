@@ -148,6 +148,13 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
     // per-tile bins of the cached bucket entries: starts, and counts / write cursors
     __shared__ uint32_t s_bstart[kMaxSegTiles + 1], s_bcnt[kMaxSegTiles + 1];
     const uint32_t tile_s = (uint32_t)__cvta_generic_to_shared(tile);  // the tile's shared-window address
+    // bytes of the tile region, for the bounds-checked build (BNX_GUARD)
+    const uint32_t tile_bytes = (uint32_t)(lay.spp - lay.tile);
+    unsigned int *const gerr = &P.ctr->err;
+    // a strike at a shared-window address inside the tile
+    auto red_tile = [&](uint32_t addr, uint32_t v) {
+        if (BNX_GUARD(addr - tile_s <= tile_bytes - 4u, gerr)) red_add_shared(addr, v);
+    };
     // the CTA's next queue segment: index, interval, interval record and bucket range
     __shared__ unsigned long long s_seg, s_b0, s_b1;
     __shared__ IvDev s_ivd;
@@ -317,6 +324,7 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
         }
         const uint32_t ntl = (seg_len + LT - 1) >> tile_log2;  // tiles of this segment (<= kMaxSegTiles)
         for (uint32_t e = tid; e < nbc; e += NT) {
+            if (!BNX_GUARD(b0 + e < P.bucket_cap && e < (uint32_t)kLogBucketCache, gerr)) continue;
             const uint32_t w = pack_hit<VB>(P.bent[b0 + e]);
             bcache[e] = w;
             const uint32_t o = w >> 12, t1 = o >> tile_log2;
@@ -341,8 +349,15 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
         for (uint32_t e = tid; e < nbc; e += NT) {
             const uint32_t w = bcache[e];
             const uint32_t o = w >> 12, t1 = o >> tile_log2;
-            if (t1 < ntl) bsort[atomicAdd(&s_bcnt[t1], 1u)] = w;
-            if ((o & (LT - 1)) == 0 && t1 >= 1) bsort[atomicAdd(&s_bcnt[t1 - 1], 1u)] = w;
+            constexpr uint32_t kBsort = kLogBucketCache + kMaxSegTiles;
+            if (t1 < ntl) {
+                const uint32_t at = atomicAdd(&s_bcnt[t1], 1u);
+                if (BNX_GUARD(at < kBsort, gerr)) bsort[at] = w;
+            }
+            if ((o & (LT - 1)) == 0 && t1 >= 1) {
+                const uint32_t at = atomicAdd(&s_bcnt[t1 - 1], 1u);
+                if (BNX_GUARD(at < kBsort, gerr)) bsort[at] = w;
+            }
         }
         const uint32_t nsparse = s_nsparse, nruns = s_nruns[warp];
         const uint32_t kinds = iv.kinds;
@@ -381,10 +396,12 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
                     constexpr uint32_t NS = NT / 81u * 81u;
                     if (tid < NS) {
                         const uint4 e = s_pat[(uint32_t)((t_lo * 76ull + tid) % 81ull)];
-                        for (uint32_t i = tid; i < n4; i += NS) t4[i] = e;
+                        for (uint32_t i = tid; i < n4; i += NS)
+                            if (BNX_GUARD(16u * (i + 1) <= tile_bytes, gerr)) t4[i] = e;
                     }
                 } else {
-                    for (uint32_t i = tid; i < n4; i += NT) t4[i] = z;
+                    for (uint32_t i = tid; i < n4; i += NT)
+                        if (BNX_GUARD(16u * (i + 1) <= tile_bytes, gerr)) t4[i] = z;
                 }
             }
             __syncthreads();
@@ -403,7 +420,7 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
                     sv0 = d.y << ((x & (VPW - 1)) * VBITS);
                 }
             }
-            if (sp0) red_add_shared(sa0, sv0);
+            if (sp0) red_tile(sa0, sv0);
             // this warp's runs of dense rounds
             for (uint32_t k = 0; k < nruns; k++) {
                 const uint32_t run = s_runs[warp][k];
@@ -423,10 +440,10 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
                     const uint32_t bstep = ((32 >> VSH) * q) << 2;
                     // rounds bounded by the lane's last address alone (no trip count), two per step
                     for (; a + bstep <= alim; a += 2 * bstep) {
-                        red_add_shared(a, lg);
-                        red_add_shared(a + bstep, lg);
+                        red_tile(a, lg);
+                        red_tile(a + bstep, lg);
                     }
-                    if (a <= alim) red_add_shared(a, lg);
+                    if (a <= alim) red_tile(a, lg);
                 }
             }
             // packed slots of the single-round prime powers
@@ -435,7 +452,7 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
                     const uint32_t e = sched[sl];
                     const uint4 d = sdesc[e & 255u];
                     const uint32_t x = d.z + (e >> 8) * d.x;
-                    if (x <= tl) red_add_shared(tile_s + ((x >> VSH) << 2), d.y << ((x & (VPW - 1)) * VBITS));
+                    if (x <= tl) red_tile(tile_s + ((x >> VSH) << 2), d.y << ((x & (VPW - 1)) * VBITS));
                 }
             }
             for (uint32_t e = s_bstart[t0 >> tile_log2] + tid, e1 = s_bstart[(t0 >> tile_log2) + 1]; e < e1; e += NT) {
@@ -443,15 +460,17 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
                 const uint32_t x = (w >> 12) - t0;
                 if (x <= tl) {
                     const uint32_t lg = cache_to_tile<VB>(w & 0xfffu);
-                    red_add_shared(tile_s + ((x >> VSH) << 2), lg << ((x & (VPW - 1)) * VBITS));
+                    red_tile(tile_s + ((x >> VSH) << 2), lg << ((x & (VPW - 1)) * VBITS));
                 }
             }
             for (unsigned long long e = b0 + nbc + tid; e < b1; e += NT) {
+                if (!BNX_GUARD(e < P.bucket_cap, gerr)) break;
                 const uint2 h = P.bent[e];
                 if (h.x >= t0 && h.x <= t0 + tl) {
                     const uint32_t x = h.x - t0;
                     const uint32_t lg = bucket_weight<VB>(h.y);
-                    atomicAdd(&tile[x >> VSH], lg << ((x & (VPW - 1)) * VBITS));
+                    if (BNX_GUARD((x >> VSH) < tile_bytes / 4u, gerr))
+                        atomicAdd(&tile[x >> VSH], lg << ((x & (VPW - 1)) * VBITS));
                 }
             }
             __syncthreads();
@@ -482,8 +501,9 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
                 if (has) {
                     n = t_lo + i;
                     const uint32_t e2 = ctz64(n + (n & 1)) - 1;  // power of 2 in P
-                    const uint32_t L0 = (tile[i >> VSH] >> ((i & (VPW - 1)) * VBITS)) & VMASK;
-                    const uint32_t L1 = (tile[(i + 1) >> VSH] >> (((i + 1) & (VPW - 1)) * VBITS)) & VMASK;
+                    const bool in_tile = BNX_GUARD(((i + 1) >> VSH) < tile_bytes / 4u, gerr);
+                    const uint32_t L0 = in_tile ? (tile[i >> VSH] >> ((i & (VPW - 1)) * VBITS)) & VMASK : 0u;
+                    const uint32_t L1 = in_tile ? (tile[(i + 1) >> VSH] >> (((i + 1) & (VPW - 1)) * VBITS)) & VMASK : 0u;
                     // log2 P <= (L0 + L1) / F + e2 must reach `need`
                     const int64_t ub = (int64_t)(L0 + L1) * FD + (int64_t)e2 * FN;
                     int need;
@@ -522,7 +542,9 @@ __global__ void __launch_bounds__(NT, LogMinBlocks<NT, VB>::value) k_sieve_log(P
                 const uint32_t g = base + tid;
                 const uint32_t ibase = kSplit ? ((g >> 5) << 10) + ((g & 31u) << 4) : G * g;
                 uint32_t cm = 0;  // candidates among the group's n (bit u: n = t_lo + ibase + uoff(u))
-                if (g < ngroups) {
+                // the group's furthest read: the word after its last chunk
+                const uint32_t g_end = kSplit ? ibase + 532u : VB == 4 ? 16u * g + 20u : 32u * g + 36u;
+                if (g < ngroups && BNX_GUARD(g_end <= tile_bytes, gerr)) {
                     uint32_t ss[G];
                     bool logc;
                     if constexpr (VB == 4) {
@@ -643,7 +665,7 @@ __global__ void __launch_bounds__(256) k_cand(Plan P) {
             const Cand cd = P.cand[c];
             n = cd.n;
             iv = cd.iv;
-            const unsigned long long ge = cd.b0 + cd.nb;
+            const unsigned long long ge = BNX_GUARD(cd.b0 + cd.nb <= P.bucket_cap, &P.ctr->err) ? cd.b0 + cd.nb : cd.b0;
             const uint64_t s0 = sodd_exact(n, cd.o, &sprimes, P.sqrt_q, P.bent, cd.b0, ge);
             const uint64_t s1 = sodd_exact(n + 1, cd.o + 1, &sprimes, P.sqrt_q, P.bent, cd.b0, ge);
             kk = exact_kinds_log(n, s0, s1, cd.kinds, MODE, P.hash_S, &a, &b);
