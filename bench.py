@@ -170,9 +170,15 @@ def dist_init():
     rank = int(os.environ.get("RANK", "0"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if ws > 1:
+        from datetime import timedelta
+
         import torch.distributed as dist
 
-        dist.init_process_group("nccl" if os.environ.get("BNX_BENCH_BACKEND") != "gloo" else "gloo")
+        # a rank that is lost (its process gone between steps) ends the others' next
+        # collective with an error after this long, instead of a hang
+        timeout = timedelta(seconds=float(os.environ.get("BNX_BENCH_PG_TIMEOUT_S", "600")))
+        dist.init_process_group("nccl" if os.environ.get("BNX_BENCH_BACKEND") != "gloo" else "gloo",
+                                timeout=timeout)
     return ws, rank, local
 
 

@@ -45,3 +45,46 @@ def test_two_ranks_shard_without_exchange():
     assert t0 == t1 == float(n0 + n1)        # value counts every rank's integers
     assert s0 == s1 == 2.0                   # time = the slowest rank
     assert all(2**32 <= lo < 2**40 and 2**16 <= hi - lo <= 2**30 for lo, hi, _ in iv0 + iv1)
+
+
+def _lost_worker(rank, world, port, out):
+    import time
+
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
+                      BNX_BENCH_BACKEND="gloo", BNX_BENCH_PG_TIMEOUT_S="10")
+    import bench
+
+    ws, r, _ = bench.dist_init()
+    bench.barrier(ws)  # both ranks up: the first step starts
+    if r == 1:
+        os._exit(3)  # the device is lost between steps: the process is gone
+    t0 = time.time()
+    try:
+        bench.max_over_ranks(ws, 1.0)  # the job's timing reduction after the step
+        out.put(("no error", time.time() - t0))
+    except Exception as e:  # noqa: BLE001 -- any error ends the wait, which is the point
+        out.put((type(e).__name__, time.time() - t0))
+    os._exit(0)
+
+
+def test_lost_rank_ends_the_next_reduction_with_an_error():
+    """A rank whose device is lost leaves between steps (its process exits); the other
+    rank learns of it on the host: its next timing reduction fails with an error within
+    the process group's timeout instead of hanging (gloo ranks on CPU, no GPU)."""
+    import multiprocessing as mp
+    import socket
+
+    ctx = mp.get_context("spawn")
+    q = ctx.Queue()
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    procs = [ctx.Process(target=_lost_worker, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    what, waited = q.get(timeout=120)
+    for p in procs:
+        p.join(timeout=60)
+    assert procs[1].exitcode == 3 and procs[0].exitcode == 0
+    assert what != "no error", what
+    assert waited < 60, waited
