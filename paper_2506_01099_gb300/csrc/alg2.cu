@@ -233,9 +233,39 @@ __global__ void __launch_bounds__(kOsThreads, 2)
 // is found from x by comparing h[x] with the records after it while the prefix
 // holds.  Each pair is found once, from its first record (Algorithm 2 compares
 // only neighbours, which would lose pairs in runs of three or more).  A warp
-// streams a contiguous chunk of 32 * 32 records with one coalesced load per
-// round; the record after a lane's comes by shuffle.
+// streams a contiguous chunk of 32 * 32 records, one coalesced load per round,
+// eight rounds' loads (and the next round's, for the last record's neighbour) in
+// flight before any is compared; the record after a lane's comes by shuffle.
 constexpr uint32_t kGroupRounds = 32;
+constexpr uint32_t kGroupBatch = 8;  // rounds loaded before they are compared
+__device__ __forceinline__ void a2_pairs_from(uint64_t x, unsigned long long hx, unsigned long long hy,
+                                              const unsigned long long *key, const uint32_t *val, uint64_t N,
+                                              const uint64_t *rad, uint32_t kinds, PairDev *pairs, uint64_t cap,
+                                              unsigned long long *np, unsigned int *err) {
+    for (uint64_t y = x + 1; (hy >> kLowBits) == (hx >> kLowBits);) {
+        if (hy == hx) {
+            const uint64_t u = val[x], w = val[y];
+            const uint64_t m = u < w ? u : w, n = u < w ? w : u;
+            const uint32_t kind = rad[m - 1] == rad[n - 1] ? 1u : 2u;  // Algorithm 2's rule
+            if (kinds & kind) {
+                const unsigned long long at = atomicAdd(np, 1ull);
+                if (at < cap) {
+                    PairDev pr;
+                    pr.m = m;
+                    pr.n = n;
+                    pr.kind = kind;
+                    pr.iv = 0;
+                    pairs[at] = pr;
+                } else {
+                    atomicOr(err, 2u);
+                }
+            }
+        }
+        if (++y >= N) break;
+        hy = key[y];
+    }
+}
+
 __global__ void k_a2_groups(const unsigned long long *key, const uint32_t *val, uint64_t N, const uint64_t *rad,
                             uint32_t kinds, PairDev *pairs, uint64_t cap, unsigned long long *np, unsigned int *err) {
     if (*(volatile unsigned int *)err & kErrLookbackAll) return;  // the sort is incomplete
@@ -244,33 +274,21 @@ __global__ void k_a2_groups(const unsigned long long *key, const uint32_t *val, 
     const uint64_t chunk = 32ull * kGroupRounds;
     for (uint64_t c0 = (((uint64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5) * chunk; c0 < N;
          c0 += nwarps * chunk) {
-        for (uint32_t r = 0; r < kGroupRounds; r++) {
-            const uint64_t x = c0 + (uint64_t)r * 32 + lane;
-            const unsigned long long hx = x < N ? key[x] : 0ull;
-            unsigned long long hy = __shfl_down_sync(0xffffffffu, hx, 1);
-            if (x + 1 >= N) continue;
-            if (lane == 31) hy = key[x + 1];
-            for (uint64_t y = x + 1; (hy >> kLowBits) == (hx >> kLowBits);) {
-                if (hy == hx) {
-                    const uint64_t u = val[x], w = val[y];
-                    const uint64_t m = u < w ? u : w, n = u < w ? w : u;
-                    const uint32_t kind = rad[m - 1] == rad[n - 1] ? 1u : 2u;  // Algorithm 2's rule
-                    if (kinds & kind) {
-                        const unsigned long long at = atomicAdd(np, 1ull);
-                        if (at < cap) {
-                            PairDev pr;
-                            pr.m = m;
-                            pr.n = n;
-                            pr.kind = kind;
-                            pr.iv = 0;
-                            pairs[at] = pr;
-                        } else {
-                            atomicOr(err, 2u);
-                        }
-                    }
-                }
-                if (++y >= N) break;
-                hy = key[y];
+        for (uint32_t r0 = 0; r0 < kGroupRounds; r0 += kGroupBatch) {
+            unsigned long long h[kGroupBatch + 1];
+#pragma unroll
+            for (uint32_t j = 0; j <= kGroupBatch; j++) {
+                const uint64_t x = c0 + (uint64_t)(r0 + j) * 32 + lane;
+                h[j] = x < N ? key[x] : 0ull;
+            }
+#pragma unroll
+            for (uint32_t j = 0; j < kGroupBatch; j++) {
+                const uint64_t x = c0 + (uint64_t)(r0 + j) * 32 + lane;
+                unsigned long long hy = __shfl_down_sync(0xffffffffu, h[j], 1);
+                const unsigned long long next0 = __shfl_sync(0xffffffffu, h[j + 1], 0);  // record x + 1 of lane 31
+                if (lane == 31) hy = next0;
+                if (x + 1 < N && (hy >> kLowBits) == (h[j] >> kLowBits))
+                    a2_pairs_from(x, h[j], hy, key, val, N, rad, kinds, pairs, cap, np, err);
             }
         }
     }
