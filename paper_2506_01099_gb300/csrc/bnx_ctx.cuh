@@ -1,6 +1,7 @@
 // The context object behind the opaque bnx_ctx handle (internal).
 #pragma once
 #include <atomic>
+#include <new>
 #include <cstdint>
 #include <mutex>
 #include <string>
@@ -43,6 +44,19 @@ struct SieveCfg {
 };
 
 int fail(int code, const char *fmt, ...);
+
+// An entry point's body; a C++ exception (a failed host allocation) becomes an error code,
+// so that none crosses the C ABI.
+template <class F>
+int guarded(F &&body) noexcept {
+    try {
+        return body();
+    } catch (const std::bad_alloc &) {
+        return fail(BNX_E_NOMEM, "host allocation failed");
+    } catch (...) {
+        return fail(BNX_E_STATE, "unexpected host error");
+    }
+}
 int grow(DevBuf &b, size_t bytes);
 void release(DevBuf &b);
 

@@ -660,7 +660,7 @@ int bnx_tune_parse(const char *json, bnx_tune *out) {
     return rc;
 }
 
-int bnx_create(bnx_ctx **out, int device, uint64_t max_hi, const char *tune_json, void *stream) {
+static int bnx_create_impl(bnx_ctx **out, int device, uint64_t max_hi, const char *tune_json, void *stream) {
     if (!out) return fail(BNX_E_ARG, "out is NULL");
     *out = nullptr;
     if (max_hi < 4 || max_hi > BNX_MAX_HI) return fail(BNX_E_ARG, "max_hi must be in [4, 2^42]");
@@ -706,6 +706,10 @@ int bnx_create(bnx_ctx **out, int device, uint64_t max_hi, const char *tune_json
     }
     *out = c;
     return BNX_OK;
+}
+
+int bnx_create(bnx_ctx **out, int device, uint64_t max_hi, const char *tune_json, void *stream) {
+    return guarded([&] { return bnx_create_impl(out, device, max_hi, tune_json, stream); });
 }
 
 void bnx_destroy(bnx_ctx *c) {
@@ -988,15 +992,20 @@ static int read_checkpoint(const char *path, CkptHeader *h, std::vector<bnx_pair
         return fail(BNX_E_ARG, "cannot open checkpoint %s", path);
     }
     int rc = BNX_OK;
-    if (fread(h, sizeof *h, 1, f) != 1 || memcmp(h->magic, kCkptMagic, 8) != 0 || h->next < h->lo ||
-        h->next > h->hi || h->npairs > ((uint64_t)1 << 40)) {
+    long size = -1;  // the file's length, checked against its header before anything is allocated
+    if (fseek(f, 0, SEEK_END) == 0) size = ftell(f);
+    rewind(f);
+    if (size < (long)sizeof *h || fread(h, sizeof *h, 1, f) != 1 || memcmp(h->magic, kCkptMagic, 8) != 0 ||
+        h->next < h->lo || h->next > h->hi) {
         rc = fail(BNX_E_ARG, "%s is not a checkpoint of this library", path);
+    } else if (h->npairs != ((uint64_t)size - sizeof *h) / sizeof(bnx_pair) ||
+               ((uint64_t)size - sizeof *h) % sizeof(bnx_pair) != 0) {
+        rc = fail(BNX_E_ARG, "checkpoint %s: %llu pairs in the header, %ld bytes in the file", path,
+                  (unsigned long long)h->npairs, size);
     } else {
-        pairs.resize(h->npairs);
+        pairs.resize(h->npairs);  // the size matches the file (an allocation failure is caught outside)
         if (h->npairs && fread(pairs.data(), sizeof(bnx_pair), h->npairs, f) != h->npairs)
             rc = fail(BNX_E_ARG, "checkpoint %s is truncated", path);
-        else if (fgetc(f) != EOF)
-            rc = fail(BNX_E_ARG, "checkpoint %s has trailing bytes", path);
     }
     fclose(f);
     if (rc == BNX_OK) *found = true;
@@ -1019,8 +1028,8 @@ static int write_checkpoint(const char *path, const CkptHeader &h, const std::ve
     return BNX_OK;
 }
 
-int bnx_search_checkpointed(bnx_ctx *c, uint64_t lo, uint64_t hi, uint32_t kinds, const char *path, uint64_t chunk,
-                            uint64_t max_chunks, bnx_pair *out, size_t cap, size_t *n_out, uint64_t *next) {
+static int search_checkpointed(bnx_ctx *c, uint64_t lo, uint64_t hi, uint32_t kinds, const char *path, uint64_t chunk,
+                               uint64_t max_chunks, bnx_pair *out, size_t cap, size_t *n_out, uint64_t *next) {
     if (!c || !path) return fail(BNX_E_ARG, "NULL argument");
     if (chunk < 1) return fail(BNX_E_ARG, "chunk must be >= 1");
     int rc = validate_interval(c, lo, hi, kinds);
@@ -1064,6 +1073,11 @@ int bnx_search_checkpointed(bnx_ctx *c, uint64_t lo, uint64_t hi, uint32_t kinds
     if (!pairs.empty()) memcpy(out, pairs.data(), pairs.size() * sizeof(bnx_pair));
     if (h.next < hi) return fail(BNX_E_BUSY, "stopped at %llu: call again to resume", (unsigned long long)h.next);
     return BNX_OK;
+}
+
+int bnx_search_checkpointed(bnx_ctx *c, uint64_t lo, uint64_t hi, uint32_t kinds, const char *path, uint64_t chunk,
+                            uint64_t max_chunks, bnx_pair *out, size_t cap, size_t *n_out, uint64_t *next) {
+    return guarded([&] { return search_checkpointed(c, lo, hi, kinds, path, chunk, max_chunks, out, cap, n_out, next); });
 }
 
 int bnx_batch(bnx_ctx *c, const bnx_interval *ivs, size_t k, bnx_pair *out, size_t cap, size_t *n_out,

@@ -269,13 +269,46 @@ static void serve(bnx_ctx *c) {
     }
 }
 
+// The loop thread: a C++ exception in it (a failed host allocation) fails every request
+// not yet finished and ends the loop, instead of terminating the process.
+static void serve_guarded(bnx_ctx *c) {
+    try {
+        serve(c);
+    } catch (...) {
+        const bool oom = [] {
+            try {
+                throw;
+            } catch (const std::bad_alloc &) {
+                return true;
+            } catch (...) {
+                return false;
+            }
+        }();
+        Server &S = *c->server;
+        std::lock_guard<std::mutex> lk(S.m);
+        for (auto &kv : S.all) {
+            Request &r = *kv.second;
+            if (!r.done) {
+                r.status = oom ? BNX_E_NOMEM : BNX_E_STATE;
+                r.done = true;
+                r.t_done = Clock::now();
+                S.st.completed++;
+            }
+        }
+        S.pending.clear();
+        S.active.clear();
+        S.stop = true;
+        publish_stats(c, S);
+    }
+}
+
 }  // namespace bnx
 
 using namespace bnx;
 
 extern "C" {
 
-int bnx_server_start(bnx_ctx *c, const bnx_server_cfg *cfg) {
+static int bnx_server_start_impl(bnx_ctx *c, const bnx_server_cfg *cfg) {
     if (!c || !cfg) return fail(BNX_E_ARG, "NULL argument");
     if (cfg->max_active < 1 || cfg->slice < 1) return fail(BNX_E_ARG, "max_active and slice must be >= 1");
     if (cfg->max_active > (1u << 24)) return fail(BNX_E_ARG, "max_active must be <= 2^24 (a batch's interval limit)");
@@ -301,11 +334,15 @@ int bnx_server_start(bnx_ctx *c, const bnx_server_cfg *cfg) {
     S->buf.resize(4096);
     c->server = S;
     c->serving.store(true);
-    S->th = std::thread(serve, c);
+    S->th = std::thread(serve_guarded, c);
     return BNX_OK;
 }
 
-int bnx_server_submit(bnx_ctx *c, const bnx_interval *iv, uint64_t *ticket) {
+int bnx_server_start(bnx_ctx *c, const bnx_server_cfg *cfg) {
+    return guarded([&] { return bnx_server_start_impl(c, cfg); });
+}
+
+static int bnx_server_submit_impl(bnx_ctx *c, const bnx_interval *iv, uint64_t *ticket) {
     if (!c || !iv || !ticket) return fail(BNX_E_ARG, "NULL argument");
     if (!c->serving.load() || !c->server) return fail(BNX_E_STATE, "not serving");
     int rc = validate_interval(c, iv->lo, iv->hi, iv->kinds);
@@ -326,6 +363,10 @@ int bnx_server_submit(bnx_ctx *c, const bnx_interval *iv, uint64_t *ticket) {
     S.cv.notify_one();
     *ticket = r->ticket;
     return BNX_OK;
+}
+
+int bnx_server_submit(bnx_ctx *c, const bnx_interval *iv, uint64_t *ticket) {
+    return guarded([&] { return bnx_server_submit_impl(c, iv, ticket); });
 }
 
 int bnx_server_cancel(bnx_ctx *c, uint64_t ticket) {
@@ -400,7 +441,7 @@ int bnx_server_get_stats(bnx_ctx *c, bnx_server_stats *out) {
     return BNX_OK;
 }
 
-int bnx_workspace_bytes(bnx_ctx *c, const bnx_interval *iv, size_t k, uint64_t *bytes) {
+static int bnx_workspace_bytes_impl(bnx_ctx *c, const bnx_interval *iv, size_t k, uint64_t *bytes) {
     if (!c || !bytes || (!iv && k)) return fail(BNX_E_ARG, "NULL argument");
     if (k > (1u << 24)) return fail(BNX_E_ARG, "at most 2^24 intervals per batch");
     if (c->server_running()) return fail(BNX_E_STATE, "the serving loop owns the context");
@@ -419,7 +460,11 @@ int bnx_workspace_bytes(bnx_ctx *c, const bnx_interval *iv, size_t k, uint64_t *
     return BNX_OK;
 }
 
-int bnx_autotune(bnx_ctx *c, const bnx_interval *iv, size_t k, int rounds, char *json_out, size_t json_cap) {
+int bnx_workspace_bytes(bnx_ctx *c, const bnx_interval *iv, size_t k, uint64_t *bytes) {
+    return guarded([&] { return bnx_workspace_bytes_impl(c, iv, k, bytes); });
+}
+
+static int bnx_autotune_impl(bnx_ctx *c, const bnx_interval *iv, size_t k, int rounds, char *json_out, size_t json_cap) {
     if (!c || !iv || k == 0) return fail(BNX_E_ARG, "need a context and at least one sample interval");
     if (rounds < 1) rounds = 1;
     bnx_tune best;
@@ -493,6 +538,10 @@ int bnx_autotune(bnx_ctx *c, const bnx_interval *iv, size_t k, int rounds, char 
                  best_ms);
     }
     return BNX_OK;
+}
+
+int bnx_autotune(bnx_ctx *c, const bnx_interval *iv, size_t k, int rounds, char *json_out, size_t json_cap) {
+    return guarded([&] { return bnx_autotune_impl(c, iv, k, rounds, json_out, json_cap); });
 }
 
 }  // extern "C"

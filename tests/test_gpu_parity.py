@@ -572,11 +572,14 @@ def test_search_checkpointed_resumes(B, ctx, orc, tmp_path):
     with pytest.raises(B.BnxError) as e:
         ctx.search_checkpointed(lo, hi + 1, 3, path, chunk)
     assert e.value.code == B.BNX_E_STATE
-    with open(path, "r+b") as f:  # a corrupt header
-        f.write(b"NOTACKPT")
-    with pytest.raises(B.BnxError) as e:
-        ctx.search_checkpointed(lo, hi, 3, path, chunk)
-    assert e.value.code == B.BNX_E_ARG
+    with open(path, "rb") as f:
+        good = f.read()
+    for bad in (b"NOTACKPT" + good[8:], good[:-10], good + b"x"):  # a corrupt header, cut or padded
+        with open(path, "wb") as f:
+            f.write(bad)
+        with pytest.raises(B.BnxError) as e:
+            ctx.search_checkpointed(lo, hi, 3, path, chunk)
+        assert e.value.code == B.BNX_E_ARG
 
 
 def test_server_cancel(B):

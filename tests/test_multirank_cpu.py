@@ -47,24 +47,40 @@ def test_two_ranks_shard_without_exchange():
     assert all(2**32 <= lo < 2**40 and 2**16 <= hi - lo <= 2**30 for lo, hi, _ in iv0 + iv1)
 
 
+def _report_and_exit(out, result, code):
+    # put() hands the result to a feeder thread: flush it before the process ends without
+    # running the exit handlers (a process group whose peer is gone is not torn down)
+    out.put(result)
+    out.close()
+    out.join_thread()
+    os._exit(code)
+
+
 def _lost_worker(rank, world, port, out):
     import time
 
     os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port), RANK=str(rank), WORLD_SIZE=str(world),
                       BNX_BENCH_BACKEND="gloo", BNX_BENCH_PG_TIMEOUT_S="10")
-    import bench
+    try:
+        import bench
 
-    ws, r, _ = bench.dist_init()
-    bench.barrier(ws)  # both ranks up: the first step starts
+        ws, r, _ = bench.dist_init()
+        bench.barrier(ws)  # both ranks up: the first step starts
+    except Exception as e:  # noqa: BLE001 -- reported, so the test fails with the reason
+        _report_and_exit(out, ("setup failed on rank %d: %r" % (rank, e), 0.0), 1)
     if r == 1:
-        os._exit(3)  # the device is lost between steps: the process is gone
+        # the device is lost between steps: once the barrier has completed on both sides
+        # (nothing of this rank is in flight), the process is gone
+        time.sleep(1.0)
+        os._exit(3)
+    time.sleep(2.0)  # this rank's step
     t0 = time.time()
     try:
         bench.max_over_ranks(ws, 1.0)  # the job's timing reduction after the step
-        out.put(("no error", time.time() - t0))
+        result = ("no error", time.time() - t0)
     except Exception as e:  # noqa: BLE001 -- any error ends the wait, which is the point
-        out.put((type(e).__name__, time.time() - t0))
-    os._exit(0)
+        result = (type(e).__name__, time.time() - t0)
+    _report_and_exit(out, result, 0)
 
 
 def test_lost_rank_ends_the_next_reduction_with_an_error():
@@ -85,6 +101,7 @@ def test_lost_rank_ends_the_next_reduction_with_an_error():
     what, waited = q.get(timeout=120)
     for p in procs:
         p.join(timeout=60)
+    assert not what.startswith("setup failed"), what
     assert procs[1].exitcode == 3 and procs[0].exitcode == 0
     assert what != "no error", what
     assert waited < 60, waited
