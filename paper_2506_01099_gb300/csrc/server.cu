@@ -298,6 +298,7 @@ static void serve_guarded(bnx_ctx *c) {
         S.pending.clear();
         S.active.clear();
         S.stop = true;
+        c->serving.store(false);  // later submits are refused; bnx_server_stop still joins and frees
         publish_stats(c, S);
     }
 }
@@ -313,7 +314,8 @@ static int bnx_server_start_impl(bnx_ctx *c, const bnx_server_cfg *cfg) {
     if (cfg->max_active < 1 || cfg->slice < 1) return fail(BNX_E_ARG, "max_active and slice must be >= 1");
     if (cfg->max_active > (1u << 24)) return fail(BNX_E_ARG, "max_active must be <= 2^24 (a batch's interval limit)");
     std::lock_guard<std::mutex> g(c->mu);
-    if (c->serving.load()) return fail(BNX_E_STATE, "already serving");
+    if (c->serving.load() || c->server)
+        return fail(BNX_E_STATE, "already serving (a loop that ended on an error is released by bnx_server_stop)");
     cudaSetDevice(c->device);
     Server *S = new (std::nothrow) Server();
     if (!S) return fail(BNX_E_NOMEM, "host allocation failed");
